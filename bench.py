@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Benchmark: batched mixed-precision ODWF D^dag D solves on one GB300.
+
+One step solves the 16^3 x 32 x Ns=16 workload's three systems (m_q = 0.002, 0.04, 0.5,
+one Gaussian right-hand side each) to a true residual of 1e-10 with the batched mixed-
+precision CG (FP16 storage with per-site scales, FP32 links of 12 reals, FP32 arithmetic,
+FP64 reliable updates), as one odwf_cg_solve_batched call.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--prec f16|bf16|f32]
+
+--impl reference times the FP64 CPU oracle (a bounded sample per step, see cpu_baseline).
+Under torchrun (N > 1) every rank runs an independent replica of the workload (the solve
+does not shard); value = all ranks' solves / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import signal
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ODWF D†D solves/s & Dslash HBM GB/s vs FP64 CG; p50/p99 served latency"
+DIMS = (16, 16, 16, 32)
+NS = 16
+M0 = 1.3
+MASSES = (0.002, 0.04, 0.5)
+EPS = 0.25
+GAUGE_SEED = 2
+RHS_SEED = 100
+LRANGE = (0.05, 6.2)
+TOL = 1e-10
+WORKLOAD = "odwf_dagd_16x16x16x32_ns16_3mass"
+ORACLE_COUNTS = os.path.join(ROOT, "tests", "golden", "oracle_cg_16x16x16x32_ns16.json")
+NCU_TRAFFIC = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+L2_FLUSH_BYTES = 512 << 20
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_inputs():
+    import odwf_synth as syn
+    from oracle import zolotarev
+
+    U = syn.gauge_field(DIMS, EPS, GAUGE_SEED)
+    w, _ = zolotarev.omega(NS, LRANGE[0], LRANGE[1], True)
+    bs = [syn.gaussian_spinor_even(NS, DIMS, RHS_SEED + k) for k in range(len(MASSES))]
+    return U, w, bs
+
+
+def oracle_iteration_counts():
+    """The oracle's own CG iteration counts on this workload (tests/golden, oracle-only script)."""
+    if not os.path.exists(ORACLE_COUNTS):
+        return None
+    d = json.load(open(ORACLE_COUNTS))
+    by = {s["mq"]: s for s in d["systems"]}
+    if not all(m in by for m in MASSES):
+        return None
+    return [by[m]["iters"] for m in MASSES], any(by[m]["capped"] for m in MASSES)
+
+
+def oracle_seconds_per_iteration(U, w, b, mq):
+    """Bounded sample: one oracle CG iteration (its initial residual, one iteration and the
+    final true residual are three S^dag S applications; the time is divided by three)."""
+    import oracle
+
+    t = time.perf_counter()
+    oracle.cg(U, b, M0, mq, w, tol=1e-30, max_iter=1)
+    return (time.perf_counter() - t) / 3.0, oracle.num_threads()
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_class):
+    """dram bytes per launch for a kernel class from the committed ncu summary, if present."""
+    if not os.path.exists(NCU_TRAFFIC):
+        return None
+    for line in open(NCU_TRAFFIC):
+        parts = line.split()
+        if len(parts) >= 2 and not line.startswith("#") and parts[0] == kernel_class:
+            try:
+                return float(parts[1])
+            except ValueError:
+                return None
+    return None
+
+
+def read_profile(lib):
+    import ctypes
+
+    from paper_1811_08095_gb300 import _lib
+
+    arr = (_lib.odwf_kernel_prof * 64)()
+    n = ctypes.c_int(0)
+    _lib.check(lib.odwf_profile_read(ctypes.cast(arr, ctypes.c_void_p), 64, ctypes.byref(n)))
+    out = []
+    for i in range(n.value):
+        e = arr[i]
+        out.append({"name": e.name.decode(), "launches": e.launches, "system_launches": e.system_launches,
+                    "total_ms": e.total_ms, "bytes_per_system": e.bytes_per_system,
+                    "bytes_per_launch": e.bytes_per_launch})
+    return out
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1811_08095_gb300 as odwf
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    lib = odwf.load()
+    stream = torch.cuda.current_stream()
+
+    U, w, bs_host = workload_inputs()
+    h = odwf.Handle(DIMS, NS, M0, MASSES[0], w)
+    h.set_gauge(torch.from_numpy(U).to(dev))
+    bs = [torch.from_numpy(b).to(dev) for b in bs_host]
+    xs = [torch.zeros_like(b) for b in bs]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(prec):
+        return h.cg_solve_batched(xs, bs, list(MASSES), tol=TOL, max_iter=200000, prec=prec, stream=stream)
+
+    for _ in range(args.warmup):
+        stats = step(args.prec)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed between steps, CUDA events on the solve's stream
+    lib.odwf_profile_enable(1)
+    launches0 = lib.odwf_launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = []
+    all_stats = []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step(args.prec)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        all_stats.append(st)
+    torch.cuda.synchronize()
+    wall_s = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = lib.odwf_launch_count() - launches0
+    prof = read_profile(lib)
+    lib.odwf_profile_enable(0)
+
+    t_total = sum(step_ms) / 1e3
+    if dist:
+        tt = torch.tensor([t_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    nsolves = len(MASSES) * args.steps * world
+    value = nsolves / t_total
+    for st in all_stats:
+        for s in st:
+            assert s["status"] == 0 and s["true_resid"] <= TOL, s
+
+    # ---- roofline of the dominant kernel (largest total time) from the in-library events
+    peak, peak_kind = measured_peaks()
+    dom = max(prof, key=lambda e: e["total_ms"]) if prof else None
+    roof = None
+    hops = {}
+    for e in prof:
+        tot_bytes = e["system_launches"] * e["bytes_per_system"] + e["launches"] * e["bytes_per_launch"]
+        gbs = tot_bytes / (e["total_ms"] / 1e3) / 1e9 if e["total_ms"] > 0 else 0.0
+        hops[e["name"]] = {"launches": e["launches"], "avg_us": 1e3 * e["total_ms"] / max(1, e["launches"]),
+                           "gbs": round(gbs, 1), "share_of_step": round(e["total_ms"] / sum(step_ms), 4)}
+    if dom:
+        per_launch = (dom["system_launches"] * dom["bytes_per_system"] + dom["launches"] * dom["bytes_per_launch"]) \
+            / dom["launches"]
+        avg_s = dom["total_ms"] / dom["launches"] / 1e3
+        achieved = per_launch / avg_s / 1e9
+        tr = ncu_traffic(dom["name"])
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": tr, "kernel": dom["name"],
+                "algorithmic_bytes_per_launch": per_launch, "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)"}
+
+    # ---- end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    bh = [torch.from_numpy(b).pin_memory() for b in bs_host]
+    xh = [torch.zeros_like(b).pin_memory() for b in bh]
+    h2d = sum(b.numel() * b.element_size() for b in bh)
+    d2h = sum(x.numel() * x.element_size() for x in xh)
+    h.cg_solve_batched([x.numpy() for x in xh], [b.numpy() for b in bh], list(MASSES), tol=TOL, max_iter=200000,
+                       prec=args.prec, stream=stream)  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        h.cg_solve_batched([x.numpy() for x in xh], [b.numpy() for b in bh], list(MASSES), tol=TOL,
+                           max_iter=200000, prec=args.prec, stream=stream)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": round(len(MASSES) * args.steps * world / e2e_s, 4), "unit": "solves/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # ---- the FP64 GPU CG on the same systems (the comparison baseline of the metric)
+    fp64 = None
+    if not args.skip_fp64:
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st64 = step("f64")
+        e1.record(stream)
+        e1.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        fp64 = {"value": round(len(MASSES) / t64, 4), "unit": "solves/s", "iters": [s["iters"] for s in st64],
+                "true_resid": [s["true_resid"] for s in st64], "speedup_mixed_vs_fp64": round(value / world /
+                                                                                             (len(MASSES) / t64), 2)}
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        counts = oracle_iteration_counts()
+        spi, cores = oracle_seconds_per_iteration(U, w, bs_host[1], MASSES[1])
+        if counts:
+            iters, capped = counts
+            src = "the oracle's own CG iteration counts %s (tests/golden, %s)" % (
+                iters, "lower bounds: capped runs" if capped else "converged runs")
+        else:
+            iters = [s["iters"] for s in (fp64 and st64 or all_stats[-1])]
+            src = "the FP64 CG iteration counts measured on the GPU in this run %s" % iters
+        cpu = {"value": round(len(MASSES) / (spi * sum(iters)), 8), "unit": "solves/s", "cores": cores,
+               "kind": "oracle",
+               "sample": "one FP64 oracle CG iteration on the same 16^3x32x16 workload (m_q=0.04; %.1f s per "
+                         "iteration on %d threads), scaled by %s" % (spi, cores, src)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(sum(step_ms) / len(step_ms), 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": "16^3x32", "Ns": NS, "m0": M0, "masses": list(MASSES),
+                       "rhs": "one unit-Gaussian right-hand side per mass (seeds 100-102)",
+                       "gauge": "U = exp(0.25 i H), H Gaussian traceless Hermitian (seed 2)",
+                       "omega": "shifted (R5) Zolotarev on [0.05, 6.2]", "tol": TOL,
+                       "precision": "%s storage (per-site FP32 scale), FP32 links (12 reals), FP32 arithmetic, "
+                                    "FP64 reliable updates and reductions" % args.prec,
+                       "solver": "batched even-odd CG on S^dag S, 3 systems per launch",
+                       "l2": "flushed between steps (512 MB write); per-system working set > 1 GB",
+                       "parallelism": "replicas only" if world > 1 else "single GPU",
+                       "iters": [s["iters"] for s in all_stats[-1]],
+                       "reliable_updates": [s["n_reliable"] for s in all_stats[-1]],
+                       "true_resid": [s["true_resid"] for s in all_stats[-1]],
+                       "wall_s_timed_region": round(wall_s, 3)},
+            "roofline": roof, "kernels": hops, "fp64_cg": fp64, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args, world, rank, local):
+    """The oracle (FP64 CPU program) on host cores: each step is one oracle CG iteration on the
+    workload, scaled to solves/s by the oracle's own iteration counts (tests/golden)."""
+    if rank != 0:
+        return
+    U, w, bs = workload_inputs()
+    counts = oracle_iteration_counts()
+    if counts is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle iteration counts for this workload not "
+                                                              "recorded (tests/golden/make_oracle_counts.py)"}))
+        return
+    iters, capped = counts
+    times = []
+    cores = 1
+    for i in range(args.warmup + args.steps):
+        spi, cores = oracle_seconds_per_iteration(U, w, bs[1], MASSES[1])
+        if i >= args.warmup:
+            times.append(spi)
+    spi = sum(times) / len(times)
+    value = len(MASSES) / (spi * sum(iters))
+    sample = ("per step one FP64 oracle CG iteration on the 16^3x32x16 workload (m_q=0.04), scaled by the "
+              "oracle's CG iteration counts %s%s" % (iters, " (lower bounds: capped runs)" if capped else ""))
+    line = {"metric": METRIC, "value": round(value, 8), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(spi * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "lattice": "16^3x32", "Ns": NS, "masses": list(MASSES), "tol": TOL},
+            "cpu_baseline": {"value": round(value, 8), "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 8), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="f16", choices=["f16", "bf16", "f32"])
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank, local)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,279 @@
+/*
+ * odwf.h -- C ABI of the GB300 optimal domain-wall fermion (ODWF) solver library.
+ *
+ * The library applies the 5D ODWF operator of Chiu, "Simulation of dynamical
+ * (u,d,s,c) domain-wall/overlap quarks at the physical point" (LATTICE2018), Sec. 2,
+ *
+ *   (D psi)_s = (rho_s D_w + 1) psi_s + (sigma_s D_w - 1) (L psi)_s,   s = 1..Ns,
+ *   D_w psi(x) = (4 - m0) psi(x) - 1/2 sum_mu [(1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                                             + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu)],
+ *   L = P_+ L_+ + P_- L_-,  (L_+ psi)_s = psi_{s-1} (s > 1), (L_+ psi)_1 = -r psi_Ns,
+ *                           (L_- psi)_s = psi_{s+1} (s < Ns), (L_- psi)_Ns = -r psi_1,
+ *   r = m_q / (2 m0),  P_+- = (1 +- gamma_5)/2,
+ *
+ * with the paper's c = 1, d = 0 (rho_s = sigma_s = omega_s, the optimal weights),
+ * its adjoint D^dag, and even-odd preconditioned conjugate-gradient solves of the
+ * Hermitian positive-definite normal equations that the pseudofermion forces of
+ * Eq. (1)-(2) need (Sec. 2, "conjugate gradient").  Everything runs on one GPU.
+ *
+ * Conventions (all public fields are complex128, i.e. interleaved re/im doubles):
+ *   lattice   dims = {Lx, Ly, Lz, Lt}, every extent even and >= 2; site index
+ *             lex = x + Lx (y + Ly (z + Lz t)); a site is even when x+y+z+t is even.
+ *   gauge     U[mu][t][z][y][x][a][b], mu = 0..3 <-> x, y, z, t, SU(3) row a, column b.
+ *             t_antiperiodic != 0 gives hops across t = Lt-1 <-> 0 a factor -1.
+ *   spinor    FULL:       psi[s][t][z][y][x][spin][colour]          (Ns * V * 12 complex)
+ *             SCHUR_EVEN: psi[s][lex/2][spin][colour] over even sites (Ns * V/2 * 12 complex)
+ *   gammas    chiral basis: gamma_k = [[0, -i sigma_k], [i sigma_k, 0]] (k = 1..3 <-> mu = 0..2),
+ *             gamma_4 = [[0, 1], [1, 0]] (mu = 3), gamma_5 = gamma_1 gamma_2 gamma_3 gamma_4 =
+ *             diag(1, 1, -1, -1): spins 0, 1 are P_+, spins 2, 3 are P_-.
+ *   Schur     S = 1 - M^-1 H_eo M^-1 H_oe on even sites, with M the site-local part of D
+ *             (D_w -> 4 - m0) and H = D - M the parity-coupling hops.
+ *
+ * Pointers: every field argument may be device memory or host memory (pageable or
+ * pinned); the library detects which and copies host data through its own device
+ * staging buffers.  Device pointers are used in place.  The caller owns every buffer
+ * it passes; the library owns its packed links, coefficients and workspaces, all
+ * freed by odwf_destroy.  `stream` is a cudaStream_t (NULL = legacy default stream);
+ * calls with device pointers are stream-ordered, calls with host pointers return
+ * after the result is in host memory.
+ *
+ * Errors: every entry point returns an int status (ODWF_OK = 0); no exception
+ * crosses the ABI.  odwf_last_error() gives a message for the calling thread's
+ * last failure.
+ */
+#ifndef ODWF_H
+#define ODWF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    ODWF_OK = 0,
+    ODWF_EINVAL = 1,      /* bad argument (sizes, modes, pointers) */
+    ODWF_ENOMEM = 2,      /* device allocation failed / HBM budget exceeded */
+    ODWF_ENOCONV = 3,     /* solver hit max_iter before the tolerance */
+    ODWF_EBREAKDOWN = 4,  /* CG breakdown: p^dag A p <= 0 or a non-finite scalar */
+    ODWF_ETIMEOUT = 5,    /* a bounded wait ran out */
+    ODWF_ECUDA = 6,       /* a CUDA runtime call failed */
+    ODWF_PENDING = 7,     /* serving: request still queued or running */
+    ODWF_ENOTFOUND = 8    /* serving: unknown ticket or field id */
+};
+
+typedef enum { ODWF_F64 = 0, ODWF_F32 = 1, ODWF_F16 = 2, ODWF_BF16 = 3 } odwf_prec;
+
+enum { ODWF_MODE_FULL = 0, ODWF_MODE_SCHUR_EVEN = 1 };
+
+enum {
+    ODWF_SYS_SCHUR_NORMAL = 0, /* S^dag S x_e = b_e,  SCHUR_EVEN fields */
+    ODWF_SYS_FULL_NORMAL = 1,  /* D^dag D x = b,       FULL fields (two Schur solves) */
+    ODWF_SYS_FULL_DIRAC = 2    /* D x = b,             FULL fields (Schur solve + reconstruction) */
+};
+
+enum { ODWF_OMEGA_SHIFTED_R5 = 0, ODWF_OMEGA_PLAIN = 1 };
+
+typedef struct {
+    int32_t dims[4];        /* Lx, Ly, Lz, Lt */
+    int32_t t_antiperiodic; /* 1: antiperiodic in time, 0: periodic */
+} odwf_lattice;
+
+typedef struct odwf_handle odwf_handle;
+
+typedef struct {
+    double tol;         /* target true relative residual ||b - A x|| / ||b|| (e.g. 1e-10) */
+    int32_t max_iter;   /* cap on inner CG iterations (summed over restarts) */
+    int32_t prec;       /* ODWF_F64: plain FP64 CG; ODWF_F32/F16/BF16: mixed precision with that
+                           storage for the inner operator fields, FP32 arithmetic, FP64 reliable updates */
+    double delta;       /* reliable-update trigger: recompute the FP64 residual when the inner
+                           residual drops below delta x its largest value since the last update
+                           (<= 0 selects 0.1) */
+    int32_t system;     /* ODWF_SYS_* */
+    int32_t link_recon; /* mixed inner links: 12 (two rows, third reconstructed) or 18; 0 = 12 */
+    double mq;          /* quark mass for this solve; NaN keeps the handle's m_q */
+    int32_t check_every;/* host status poll interval in iterations (0 = 8) */
+    int32_t reserved;
+} odwf_solve_params;
+
+typedef struct {
+    int32_t iters;          /* inner CG iterations */
+    int32_t n_reliable;     /* FP64 residual recomputations */
+    double true_resid;      /* final ||b - A x|| / ||b||, recomputed in FP64 on the GPU */
+    double time_ms;         /* wall time of the solve inside the library */
+    int32_t status;         /* ODWF_OK / ODWF_ENOCONV / ODWF_EBREAKDOWN for this system */
+    int32_t reserved;
+} odwf_solve_stats;
+
+/* Last error message of the calling thread ("" if none). */
+const char* odwf_last_error(void);
+
+/* Library version string. */
+const char* odwf_version(void);
+
+/*
+ * Optimal weights omega_s (Sec. 2): Zolotarev's optimal rational approximation
+ * R_Z(x) of 1/sqrt(x), degree (n-1, n) for Ns = 2n, on x in [1, (lmax/lmin)^2].
+ * variant ODWF_OMEGA_SHIFTED_R5 (the paper's choice): S(H) = sqrt(x) R_Z(x)/(1 + d_Z)
+ *   with 0 <= 1 - S <= 2 d_Z; the weights are n distinct values, each twice, returned
+ *   as w_1 < ... < w_n, w_n, ..., w_1 (R5 symmetric: omega_s = omega_{Ns+1-s}).
+ * variant ODWF_OMEGA_PLAIN: S = sqrt(x) R_Z(x), |1 - S| <= d_Z, 2n distinct weights
+ *   in increasing order.
+ * omega_out: host array of Ns doubles; dz_out (may be NULL): d_Z.  Host-only, no GPU.
+ * Returns ODWF_EINVAL for odd Ns, Ns < 2, Ns > 64 or 0 < lmin < lmax violated.
+ */
+int odwf_zolotarev_omega(int Ns, double lmin, double lmax, int variant, double* omega_out,
+                         double* dz_out);
+
+/*
+ * Create a handle for one lattice, Ns, m0, default m_q and weights (Sec. 2).
+ * omega: host array of Ns doubles (rho_s = sigma_s = omega_s).  Ns must divide 32
+ * (2, 4, 8, 16 or 32).  Allocates nothing large; links come with odwf_set_gauge.
+ * *out receives the handle; ODWF_EINVAL on bad sizes, ODWF_ECUDA without a device.
+ */
+int odwf_create(const odwf_lattice* lat, int Ns, double m0, double mq, const double* omega,
+                odwf_handle** out);
+
+/* Free the handle and everything the library allocated for it. */
+int odwf_destroy(odwf_handle* h);
+
+/*
+ * Set the gauge field: U (host or device, complex128, layout above).  The library
+ * packs it into its internal parity-split arrays: FP64 with 18 reals for the FP64
+ * path and FP32 with 12 reals (third row rebuilt as conj(row1 x row2), exact for
+ * SU(3)) plus 18 reals for the mixed path.  The time-boundary sign is applied in the
+ * kernels, so the stored links stay in SU(3).  Stream-ordered on `stream`.
+ */
+int odwf_set_gauge(odwf_handle* h, const void* U, void* stream);
+
+/*
+ * out = D in (mode ODWF_MODE_FULL, full fields) or out = S in (ODWF_MODE_SCHUR_EVEN,
+ * even-site fields), in FP64.  in and out must not overlap.
+ */
+int odwf_apply(odwf_handle* h, void* out, const void* in, int mode, void* stream);
+
+/* out = D^dag in or out = S^dag in, as odwf_apply. */
+int odwf_apply_dagger(odwf_handle* h, void* out, const void* in, int mode, void* stream);
+
+/*
+ * out = A in for the normal operator of `system`: S^dag S (SCHUR_NORMAL, even fields)
+ * or D^dag D (FULL_NORMAL, full fields), FP64.
+ */
+int odwf_apply_normal(odwf_handle* h, void* out, const void* in, int system, void* stream);
+
+/*
+ * out = S^dag S in computed by the mixed-precision inner operator: in is rounded to
+ * `prec` storage (ODWF_F32, ODWF_F16 or ODWF_BF16; FP16/BF16 with one FP32 scale per 5D
+ * site), the four hops run in FP32 with FP32 links of `link_recon` (12 or 18) reals, and
+ * every intermediate field is stored in `prec`.  Even-site fields, as odwf_apply_normal.
+ * This is the operator the inner CG iterates with; it is exposed for accuracy checks.
+ */
+int odwf_apply_normal_prec(odwf_handle* h, void* out, const void* in, int prec, int link_recon, void* stream);
+
+/*
+ * Site-local part of D on a field of n_sites sites per s-slice (any sites, layout
+ * [s][site][spin][colour]): op 0 = M, 1 = M^dag, 2 = M^-1, 3 = M^-dag, in FP64.
+ * M = (4-m0) B + 1 - L with B = rho + sigma L; the inverse is an O(Ns) cyclic solve.
+ */
+int odwf_apply_m5(odwf_handle* h, void* out, const void* in, long n_sites, int op, void* stream);
+
+/*
+ * Solve one system by conjugate gradient (Sec. 2).  x: initial guess ignored, result
+ * written; b: right-hand side (layouts by system).  stats may be NULL.
+ * Returns ODWF_OK on convergence to params->tol, ODWF_ENOCONV at max_iter (x holds the
+ * last iterate), ODWF_EBREAKDOWN on a breakdown.
+ */
+int odwf_cg_solve(odwf_handle* h, void* x, const void* b, const odwf_solve_params* params,
+                  odwf_solve_stats* stats, void* stream);
+
+/*
+ * Solve nsys systems that share the handle's gauge field, Ns, m0 and weights but
+ * have their own right-hand side b[i] and mass mq[i] (mq may be NULL: the handle's
+ * m_q), in one batched launch sequence: every hop launch covers all unconverged
+ * systems and reuses each site's links across them; converged systems are masked
+ * out.  stats: array of nsys entries (may be NULL).  Returns the first non-OK
+ * per-system status, or ODWF_OK.  SCHUR_NORMAL only.
+ */
+int odwf_cg_solve_batched(odwf_handle* h, int nsys, void* const* x, const void* const* b,
+                          const double* mq, const odwf_solve_params* params,
+                          odwf_solve_stats* stats, void* stream);
+
+/* ----------------------------------------------------------------------------------
+ * Kernel timing (no counterpart in the paper; used to place the kernels on the roofline).
+ * ---------------------------------------------------------------------------------- */
+typedef struct {
+    char name[48];              /* kernel class, e.g. "mixed.f16.K4_normal_cg" */
+    int64_t launches;           /* timed launches */
+    int64_t system_launches;    /* (system, launch) pairs that ran (gated systems excluded) */
+    double total_ms;            /* summed CUDA-event time of the launches, on their stream */
+    double bytes_per_system;    /* algorithmic bytes per running system: each field read or
+                                   written once */
+    double bytes_per_launch;    /* algorithmic bytes per launch shared by all systems (links) */
+} odwf_kernel_prof;
+
+/* Start (on != 0, counters reset) or stop timing the solver's kernels.  Process-wide;
+ * adds two event records per launch. */
+int odwf_profile_enable(int on);
+
+/* Synchronize the device and copy up to max_entries kernel classes with launches into
+ * out; *n_out receives the count. */
+int odwf_profile_read(odwf_kernel_prof* out, int max_entries, int* n_out);
+
+/* Number of kernel launches the library has issued in this process (all kernels). */
+long long odwf_launch_count(void);
+
+/* ----------------------------------------------------------------------------------
+ * Serving: a request loop that keeps gauge fields resident, admits solve requests by
+ * an HBM budget into per-(field, Ns, m0, weights) batches, and solves them with
+ * continuous batching (requests join a running batch between iterations as slots and
+ * memory free up; batches of different fields run concurrently on separate streams).
+ * ---------------------------------------------------------------------------------- */
+typedef struct serve_handle serve_handle;
+
+typedef struct {
+    int32_t field_id;     /* a field registered with serve_register_gauge */
+    int32_t Ns;
+    double m0;
+    double mq;
+    const double* omega;  /* host, Ns doubles; copied at submit */
+    int32_t nrhs;
+    const void* const* b; /* nrhs host or device pointers, SCHUR_EVEN layout */
+    void* const* x;       /* nrhs output pointers, same kind as b */
+    double tol;
+    int32_t prec;         /* inner precision, as odwf_solve_params.prec */
+    int32_t max_iter;
+} odwf_request;
+
+typedef struct {
+    int32_t status;       /* ODWF_OK, ODWF_PENDING, or an error code */
+    int32_t iters;        /* largest inner iteration count over the request's systems */
+    double true_resid;    /* largest final true relative residual over its systems */
+    double latency_ms;    /* submit -> completion */
+    double queue_ms;      /* submit -> admission */
+} odwf_result;
+
+/* Create a server with a device-memory budget in bytes (0 = 90% of free memory). */
+int serve_create(size_t hbm_budget_bytes, serve_handle** out);
+
+/* Register (upload and pack) a resident gauge field under field_id. U host or device. */
+int serve_register_gauge(serve_handle* s, int field_id, const odwf_lattice* lat, const void* U);
+
+/* Queue a request; *ticket identifies it.  ODWF_ENOMEM if it can never fit the budget. */
+int serve_submit(serve_handle* s, const odwf_request* req, uint64_t* ticket);
+
+/*
+ * Wait up to timeout_ms (0 = just look) for the request.  Returns ODWF_PENDING while it
+ * is queued or running, otherwise its final status; res (may be NULL) gets the details.
+ * A finished ticket can be polled again until serve_destroy.
+ */
+int serve_poll(serve_handle* s, uint64_t ticket, int timeout_ms, odwf_result* res);
+
+/* Stop the loop after the running work, fail queued requests, free everything. */
+int serve_destroy(serve_handle* s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ODWF_H */

@@ -1,0 +1,222 @@
+"""GB300-native optimal domain-wall fermion (ODWF) operator and D^dag D solvers.
+
+Thin Python layer over the C ABI in include/odwf.h (libodwf.so, built in-tree for
+sm_103a).  Functions named like the C entry points take the same arguments; `Handle`
+and `Server` wrap them for convenience.  Every computation runs in the library's CUDA
+kernels; this module only marshals arguments.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+
+from . import _lib
+from ._lib import (ODWF_BF16, ODWF_F16, ODWF_F32, ODWF_F64, ODWF_MODE_FULL, ODWF_MODE_SCHUR_EVEN,
+                   ODWF_OMEGA_PLAIN, ODWF_OMEGA_SHIFTED_R5, ODWF_SYS_FULL_DIRAC, ODWF_SYS_FULL_NORMAL,
+                   ODWF_SYS_SCHUR_NORMAL, OdwfError, check, ptr, stream_ptr)
+
+__all__ = ["Handle", "Server", "odwf_zolotarev_omega", "OdwfError", "ODWF_F64", "ODWF_F32", "ODWF_F16",
+           "ODWF_BF16", "ODWF_MODE_FULL", "ODWF_MODE_SCHUR_EVEN", "ODWF_SYS_SCHUR_NORMAL",
+           "ODWF_SYS_FULL_NORMAL", "ODWF_SYS_FULL_DIRAC", "ODWF_OMEGA_SHIFTED_R5", "ODWF_OMEGA_PLAIN",
+           "load", "lib_path"]
+
+PREC = {"f64": ODWF_F64, "f32": ODWF_F32, "f16": ODWF_F16, "bf16": ODWF_BF16}
+
+
+def load(build_if_missing: bool = False):
+    return _lib.load(build_if_missing)
+
+
+def lib_path() -> str:
+    return _lib.LIB_PATH
+
+
+def odwf_version() -> str:
+    return _lib.load().odwf_version().decode()
+
+
+def odwf_zolotarev_omega(ns: int, lmin: float, lmax: float, variant: int = ODWF_OMEGA_SHIFTED_R5):
+    """Optimal weights omega_s (host computation).  Returns (omega[Ns], d_Z)."""
+    out = np.zeros(ns, dtype=np.float64)
+    dz = ctypes.c_double(0.0)
+    check(_lib.load().odwf_zolotarev_omega(int(ns), float(lmin), float(lmax), int(variant), ptr(out),
+                                           ctypes.byref(dz)))
+    return out, dz.value
+
+
+def _lattice(dims, t_antiperiodic):
+    lat = _lib.odwf_lattice()
+    for i in range(4):
+        lat.dims[i] = int(dims[i])
+    lat.t_antiperiodic = 1 if t_antiperiodic else 0
+    return lat
+
+
+def _params(tol, max_iter, prec, delta, system, link_recon, mq, check_every):
+    p = _lib.odwf_solve_params()
+    p.tol = float(tol)
+    p.max_iter = int(max_iter)
+    p.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    p.delta = float(delta)
+    p.system = int(system)
+    p.link_recon = int(link_recon)
+    p.mq = float("nan") if mq is None else float(mq)
+    p.check_every = int(check_every)
+    return p
+
+
+def _stats_dict(s):
+    return {"iters": s.iters, "n_reliable": s.n_reliable, "true_resid": s.true_resid, "time_ms": s.time_ms,
+            "status": s.status}
+
+
+class Handle:
+    """One lattice / Ns / m0 / weights configuration (odwf_create ... odwf_destroy)."""
+
+    def __init__(self, dims, ns, m0, mq, omega, t_antiperiodic=True):
+        self._lib = _lib.load()
+        self.dims = tuple(int(d) for d in dims)
+        self.ns = int(ns)
+        self.m0 = float(m0)
+        self.mq = float(mq)
+        self.omega = np.ascontiguousarray(omega, dtype=np.float64)
+        lat = _lattice(dims, t_antiperiodic)
+        h = ctypes.c_void_p()
+        check(self._lib.odwf_create(ctypes.byref(lat), self.ns, self.m0, self.mq, ptr(self.omega), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def volume(self):
+        return math.prod(self.dims)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.odwf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_gauge(self, U, stream=None):
+        check(self._lib.odwf_set_gauge(self._h, ptr(U), stream_ptr(stream)))
+
+    def apply(self, out, inp, mode=ODWF_MODE_FULL, stream=None):
+        check(self._lib.odwf_apply(self._h, ptr(out), ptr(inp), int(mode), stream_ptr(stream)))
+        return out
+
+    def apply_dagger(self, out, inp, mode=ODWF_MODE_FULL, stream=None):
+        check(self._lib.odwf_apply_dagger(self._h, ptr(out), ptr(inp), int(mode), stream_ptr(stream)))
+        return out
+
+    def apply_normal(self, out, inp, system=ODWF_SYS_SCHUR_NORMAL, stream=None):
+        check(self._lib.odwf_apply_normal(self._h, ptr(out), ptr(inp), int(system), stream_ptr(stream)))
+        return out
+
+    def apply_normal_prec(self, out, inp, prec="f16", link_recon=12, stream=None):
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        check(self._lib.odwf_apply_normal_prec(self._h, ptr(out), ptr(inp), p, int(link_recon), stream_ptr(stream)))
+        return out
+
+    def apply_m5(self, out, inp, n_sites, op, stream=None):
+        check(self._lib.odwf_apply_m5(self._h, ptr(out), ptr(inp), int(n_sites), int(op), stream_ptr(stream)))
+        return out
+
+    def cg_solve(self, x, b, tol=1e-10, max_iter=100000, prec="f64", delta=0.1, system=ODWF_SYS_SCHUR_NORMAL,
+                 link_recon=12, mq=None, check_every=8, stream=None, raise_on_error=True):
+        p = _params(tol, max_iter, prec, delta, system, link_recon, mq, check_every)
+        st = _lib.odwf_solve_stats()
+        rc = self._lib.odwf_cg_solve(self._h, ptr(x), ptr(b), ctypes.byref(p), ctypes.byref(st), stream_ptr(stream))
+        if raise_on_error:
+            check(rc)
+        d = _stats_dict(st)
+        d["rc"] = rc
+        return d
+
+    def cg_solve_batched(self, xs, bs, mqs=None, tol=1e-10, max_iter=100000, prec="f64", delta=0.1,
+                         link_recon=12, check_every=8, stream=None, raise_on_error=True):
+        n = len(xs)
+        assert len(bs) == n
+        xa = (ctypes.c_void_p * n)(*[ptr(x).value for x in xs])
+        ba = (ctypes.c_void_p * n)(*[ptr(b).value for b in bs])
+        mq_arr = None
+        if mqs is not None:
+            mq_np = np.ascontiguousarray(mqs, dtype=np.float64)
+            assert mq_np.shape == (n,)
+            mq_arr = ptr(mq_np)
+        p = _params(tol, max_iter, prec, delta, ODWF_SYS_SCHUR_NORMAL, link_recon, None, check_every)
+        st = (_lib.odwf_solve_stats * n)()
+        rc = self._lib.odwf_cg_solve_batched(self._h, n, ctypes.cast(xa, ctypes.c_void_p),
+                                             ctypes.cast(ba, ctypes.c_void_p), mq_arr, ctypes.byref(p),
+                                             ctypes.cast(st, ctypes.c_void_p), stream_ptr(stream))
+        if raise_on_error:
+            check(rc)
+        out = [_stats_dict(s) for s in st]
+        for d in out:
+            d["rc"] = rc
+        return out
+
+
+class Server:
+    """Serving loop (serve_create ... serve_destroy): resident gauge fields, continuous batching."""
+
+    def __init__(self, hbm_budget_bytes=0):
+        self._lib = _lib.load()
+        h = ctypes.c_void_p()
+        check(self._lib.serve_create(ctypes.c_size_t(int(hbm_budget_bytes)), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def register_gauge(self, field_id, dims, U, t_antiperiodic=True):
+        lat = _lattice(dims, t_antiperiodic)
+        check(self._lib.serve_register_gauge(self._h, int(field_id), ctypes.byref(lat), ptr(U)))
+
+    def submit(self, field_id, ns, m0, mq, omega, bs, xs, tol=1e-10, prec="f16", max_iter=100000):
+        n = len(bs)
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        ba = (ctypes.c_void_p * n)(*[ptr(b).value for b in bs])
+        xa = (ctypes.c_void_p * n)(*[ptr(x).value for x in xs])
+        req = _lib.odwf_request()
+        req.field_id = int(field_id)
+        req.Ns = int(ns)
+        req.m0 = float(m0)
+        req.mq = float(mq)
+        req.omega = om.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        req.nrhs = n
+        req.b = ctypes.cast(ba, ctypes.POINTER(ctypes.c_void_p))
+        req.x = ctypes.cast(xa, ctypes.POINTER(ctypes.c_void_p))
+        req.tol = float(tol)
+        req.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+        req.max_iter = int(max_iter)
+        t = ctypes.c_uint64(0)
+        check(self._lib.serve_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
+        self._keep[t.value] = (om, ba, xa, bs, xs)
+        return t.value
+
+    def poll(self, ticket, timeout_ms=0):
+        r = _lib.odwf_result()
+        rc = self._lib.serve_poll(self._h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(r))
+        return rc, {"status": r.status, "iters": r.iters, "true_resid": r.true_resid, "latency_ms": r.latency_ms,
+                    "queue_ms": r.queue_ms}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.serve_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,345 @@
+// Slot-based batched CG (see batch_cg.h).
+#include "batch_cg.h"
+
+#include <cmath>
+#include <cstring>
+
+namespace odwf {
+
+BatchCG::~BatchCG() {
+    if (st_host) cudaFreeHost(st_host);
+}
+
+template <>
+HopParams<double> BatchCG::params<double>(int p_out) const {
+    auto P = E->hop_params<double>(p_out, r_dev);
+    P.st = st;
+    P.partials = partials;
+    P.counters = counters;
+    return P;
+}
+
+template <>
+HopParams<float> BatchCG::params<float>(int p_out) const {
+    auto P = E->hop_params<float>(p_out, r_dev);
+    P.links = lk == Lk::F12 ? E->links_f12 : E->links_f18;
+    P.st = st;
+    P.partials = partials;
+    P.counters = counters;
+    return P;
+}
+
+int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStream_t s) {
+    E = e;
+    cap = capacity;
+    mixed = prm.prec != ODWF_F64;
+    low = (Sp)prm.prec;
+    lk = prm.link_recon == 18 ? Lk::F18 : Lk::F12;
+    delta = prm.delta > 0 ? prm.delta : 0.1;
+    tol = prm.tol;
+    max_iter = prm.max_iter;
+    int rc = 0;
+    if ((rc = E->alloc_half("cg.X64", Sp::F64, cap, &X64)) || (rc = E->alloc_half("cg.R64", Sp::F64, cap, &R64)) ||
+        (rc = E->alloc_half("cg.B64", Sp::F64, cap, &B64)))
+        return rc;
+    if (!mixed) {
+        if ((rc = E->alloc_half("cg.P64", Sp::F64, cap, &P64)) || (rc = E->alloc_half("cg.T64", Sp::F64, cap, &T64)) ||
+            (rc = E->alloc_half("cg.A64", Sp::F64, cap, &A64)) || (rc = E->alloc_half("cg.C64", Sp::F64, cap, &C64)))
+            return rc;
+    } else {
+        const std::string tag = "cg.lo" + std::to_string((int)low);
+        if ((rc = E->alloc_half("cg.Rin", Sp::F32, cap, &Rin)) || (rc = E->alloc_half("cg.Xin", Sp::F32, cap, &Xin)) ||
+            (rc = E->alloc_half(tag + ".P", low, cap, &Pl)) || (rc = E->alloc_half(tag + ".T", low, cap, &Tl)) ||
+            (rc = E->alloc_half(tag + ".A", low, cap, &Al)) || (rc = E->alloc_half(tag + ".C", low, cap, &Cl)) ||
+            (rc = E->alloc_half("cg.T1", Sp::F64, 1, &T1)) || (rc = E->alloc_half("cg.A1", Sp::F64, 1, &A1)) ||
+            (rc = E->alloc_half("cg.C1", Sp::F64, 1, &C1)))
+            return rc;
+    }
+    st = (SysState*)E->get_ws("cg.state", sizeof(SysState) * cap, &rc);
+    if (rc) return rc;
+    r_dev = (double*)E->get_ws("cg.r", sizeof(double) * cap, &rc);
+    if (rc) return rc;
+    const int nblk = blocks_for(E->sites5(), 256);
+    partials = (double*)E->get_ws("cg.partials", sizeof(double) * (size_t)nblk * cap, &rc);
+    if (rc) return rc;
+    counters = (unsigned*)E->get_ws("cg.counters", sizeof(unsigned) * cap, &rc);
+    if (rc) return rc;
+    ODWF_CK(cudaMemsetAsync(counters, 0, sizeof(unsigned) * cap, s));
+    // pinned: state mirror [cap], initial-state staging [cap], r staging [cap]
+    if (cudaMallocHost(&st_host, 2 * sizeof(SysState) * cap + sizeof(double) * cap) != cudaSuccess) {
+        cudaGetLastError();
+        st_host = nullptr;
+        return fail(ODWF_ENOMEM, "pinned host allocation failed");
+    }
+    std::memset(st_host, 0, sizeof(SysState) * cap);
+    for (int i = 0; i < cap; ++i) st_host[i].status = kIdle;
+    ODWF_CK(cudaMemcpyAsync(st, st_host, sizeof(SysState) * cap, cudaMemcpyHostToDevice, s));
+    ODWF_CK(cudaStreamSynchronize(s));
+    n_reliable.assign(cap, 0);
+    active.assign(cap, 0);
+    mq.assign(cap, 0.0);
+    slot_tol.assign(cap, tol);
+    // profiler classes with their algorithmic bytes (each field read or written once)
+    const double n5 = (double)E->sites5();
+    const double sp = !mixed ? 192.0 : (low == Sp::F32 ? 96.0 : 52.0);  // FP16/BF16: 48 + 4-byte scale
+    const double acc = mixed ? 96.0 : 192.0;                              // r, x
+    const double links = 8.0 * (double)E->vh() * (!mixed ? 144.0 : (lk == Lk::F12 ? 48.0 : 72.0));
+    const char* lowname[] = {"f64", "f32", "f16", "bf16"};
+    const std::string pre = !mixed ? std::string("f64") :
+        std::string("mixed.") + lowname[(int)low] + (lk == Lk::F12 ? ".l12" : ".l18");
+    pcls[0] = prof_class(pre + ".K1_minv", n5 * 2 * sp, links);
+    pcls[1] = prof_class(pre + ".K2_schur_norm_mdinv", n5 * 3 * sp, links);
+    pcls[2] = prof_class(pre + ".K3_dag_minvdag", n5 * 2 * sp, links);
+    pcls[3] = prof_class(pre + ".K4_normal_cg", n5 * (3 * sp + 4 * acc), links);
+    pcls[4] = prof_class(pre + ".P_update", n5 * (acc + 2 * sp), 0.0);
+    const double l64 = 8.0 * (double)E->vh() * 144.0;
+    pcls_rel[0] = prof_class("f64.reliable.K1_minv", n5 * 2 * 192.0, l64);
+    pcls_rel[1] = prof_class("f64.reliable.K2_schur_mdinv", n5 * 3 * 192.0, l64);
+    pcls_rel[2] = prof_class("f64.reliable.K3_dag_minvdag", n5 * 2 * 192.0, l64);
+    pcls_rel[3] = prof_class("f64.reliable.K4_resid", n5 * 4 * 192.0, l64);
+    return ODWF_OK;
+}
+
+int BatchCG::admit(int slot, const double2* b_ext, double mq_slot, cudaStream_t s, double tol_slot,
+                   int max_iter_slot) {
+    if (slot < 0 || slot >= cap) return fail(ODWF_EINVAL, "admit: bad slot");
+    ODWF_CK(launch_pack(Sp::F64, b_ext, B64.ref_sys(slot), E->g, 0, E->ns, 1, s));
+    mq[slot] = mq_slot;
+    return admit_internal(slot, s, tol_slot, max_iter_slot);
+}
+
+int BatchCG::release(int slot) {
+    if (slot < 0 || slot >= cap) return fail(ODWF_EINVAL, "release: bad slot");
+    active[slot] = 0;
+    st_host[slot].status = kIdle;
+    return ODWF_OK;
+}
+
+int BatchCG::admit_internal(int slot, cudaStream_t s, double tol_slot, int max_iter_slot) {
+    const double tl = tol_slot > 0 ? tol_slot : tol;
+    slot_tol[slot] = tl;
+    const size_t n5 = E->sites5();
+    const int ns = E->ns;
+    // per-slot scalars: r = m_q / (2 m0) and a fresh state (written through pinned memory)
+    double* rpin = reinterpret_cast<double*>(st_host + 2 * cap) + slot;
+    *rpin = mq[slot] / (2.0 * E->m0);
+    ODWF_CK(cudaMemcpyAsync(r_dev + slot, rpin, sizeof(double), cudaMemcpyHostToDevice, s));
+    SysState init;
+    std::memset(&init, 0, sizeof(init));
+    init.status = kIdle;
+    init.max_iter = max_iter_slot > 0 ? max_iter_slot : max_iter;
+    init.delta = delta;
+    init.reliable = mixed ? 1 : 0;
+    SysState* stage = st_host + cap + slot;  // a slot is re-admitted only after finalize() synchronized
+    *stage = init;
+    ODWF_CK(cudaMemcpyAsync(st + slot, stage, sizeof(SysState), cudaMemcpyHostToDevice, s));
+    // ||b||^2 -> state, then rr = bb, status running
+    ODWF_CK(launch_vec(Sp::F64, Sp::F64, B64.ref(), B64.ref(), n5, ns, 3, 0.0, st, 0, 0, partials, counters, slot,
+                       1, s));
+    ODWF_CK(launch_state(st + slot, 1, 0, tl * tl, s));
+    ODWF_CK(launch_vec(Sp::F64, Sp::F64, X64.ref(), X64.ref(), n5, ns, 5, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
+    ODWF_CK(launch_vec(Sp::F64, Sp::F64, B64.ref(), R64.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
+    if (!mixed) {
+        ODWF_CK(launch_vec(Sp::F64, Sp::F64, B64.ref(), P64.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
+    } else {
+        ODWF_CK(launch_vec(Sp::F64, Sp::F32, B64.ref(), Rin.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
+        ODWF_CK(launch_vec(Sp::F32, Sp::F32, Xin.ref(), Xin.ref(), n5, ns, 5, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
+        ODWF_CK(launch_vec(Sp::F64, low, B64.ref(), Pl.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
+    }
+    active[slot] = 1;
+    n_reliable[slot] = 0;
+    st_host[slot].status = kRunning;  // host view until the next poll
+    return ODWF_OK;
+}
+
+int BatchCG::run_iterations(int k, cudaStream_t s) {
+    int lo = cap, hi = -1;
+    for (int i = 0; i < cap; ++i)
+        if (active[i] && slot_running(i)) {
+            lo = std::min(lo, i);
+            hi = std::max(hi, i);
+        }
+    if (hi < 0) return ODWF_OK;
+    const int n = hi - lo + 1;
+    const size_t n5 = E->sites5();
+    for (int it = 0; it < k; ++it) {
+        if (!mixed) {
+            auto P = params<double>(1);
+            P.gate = 1;
+            P.need_status = kRunning;
+            P.sys_base = lo;
+            P.in = P64.ref();
+            P.out = T64.ref();
+            { auto pb_ = prof_begin(pcls[0], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_f64(P, Epi::MINV, n, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+            P.p_out = 0;
+            P.in = T64.ref();
+            P.z = P64.ref();
+            P.out = A64.ref();
+            { auto pb_ = prof_begin(pcls[1], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_f64(P, Epi::SCHUR_NORM_MDINV, n, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+            P.p_out = 1;
+            P.in = A64.ref();
+            P.z = FieldRef{};
+            P.out = C64.ref();
+            { auto pb_ = prof_begin(pcls[2], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_f64(P, Epi::D_MINVDAG, n, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+            P.p_out = 0;
+            P.in = C64.ref();
+            P.z = A64.ref();
+            P.out = FieldRef{};
+            P.cg_r = R64.ref();
+            P.cg_x = X64.ref();
+            P.cg_p = P64.ref();
+            { auto pb_ = prof_begin(pcls[3], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_f64(P, Epi::D_NORMAL_CG, n, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+            {
+                auto pb_ = prof_begin(pcls[4], s);
+                set_vec_prof(pb_.dev_count);
+                cudaError_t e_ = launch_vec(Sp::F64, Sp::F64, R64.ref(), P64.ref(), n5, E->ns, 1, 0.0, st, 1, kRunning,
+                                            nullptr, nullptr, lo, n, s);
+                set_vec_prof(nullptr);
+                prof_end(pb_, s);
+                ODWF_CK(e_);
+            }
+        } else {
+            auto P = params<float>(1);
+            P.gate = 1;
+            P.need_status = kRunning;
+            P.sys_base = lo;
+            P.in = Pl.ref();
+            P.out = Tl.ref();
+            { auto pb_ = prof_begin(pcls[0], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_mixed(P, Epi::MINV, low, lk, n, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+            P.p_out = 0;
+            P.in = Tl.ref();
+            P.z = Pl.ref();
+            P.out = Al.ref();
+            { auto pb_ = prof_begin(pcls[1], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_mixed(P, Epi::SCHUR_NORM_MDINV, low, lk, n, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+            P.p_out = 1;
+            P.in = Al.ref();
+            P.z = FieldRef{};
+            P.out = Cl.ref();
+            { auto pb_ = prof_begin(pcls[2], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_mixed(P, Epi::D_MINVDAG, low, lk, n, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+            P.p_out = 0;
+            P.in = Cl.ref();
+            P.z = Al.ref();
+            P.out = FieldRef{};
+            P.cg_r = Rin.ref();
+            P.cg_x = Xin.ref();
+            P.cg_p = Pl.ref();
+            { auto pb_ = prof_begin(pcls[3], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_mixed(P, Epi::D_NORMAL_CG, low, lk, n, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+            {
+                auto pb_ = prof_begin(pcls[4], s);
+                set_vec_prof(pb_.dev_count);
+                cudaError_t e_ = launch_vec(Sp::F32, low, Rin.ref(), Pl.ref(), n5, E->ns, 1, 0.0, st, 1, kRunning,
+                                            nullptr, nullptr, lo, n, s);
+                set_vec_prof(nullptr);
+                prof_end(pb_, s);
+                ODWF_CK(e_);
+            }
+        }
+    }
+    return ODWF_OK;
+}
+
+int BatchCG::poll(cudaStream_t s) {
+    ODWF_CK(cudaMemcpyAsync(st_host, st, sizeof(SysState) * cap, cudaMemcpyDeviceToHost, s));
+    ODWF_CK(cudaStreamSynchronize(s));
+    prof_collect();
+    return ODWF_OK;
+}
+
+bool BatchCG::slot_running(int i) const {
+    const int stt = st_host[i].status;
+    return stt == kRunning || stt == kNeedUpdate;
+}
+
+bool BatchCG::slot_finished(int i) const {
+    const int stt = st_host[i].status;
+    return active[i] && (stt == kDone || stt == kBreakdown || stt == kMaxIter);
+}
+
+int BatchCG::any_running() const {
+    for (int i = 0; i < cap; ++i)
+        if (active[i] && slot_running(i)) return 1;
+    return 0;
+}
+
+// R[slot] = B[slot] - S^dag S X[slot] in FP64, |R|^2 -> st[slot].sum
+int BatchCG::fp64_residual(int slot, const HalfField& X, const HalfField& R, cudaStream_t s) {
+    FieldRef t, a, c;
+    if (mixed) {
+        t = T1.ref_shared();
+        a = A1.ref_shared();
+        c = C1.ref_shared();
+    } else {
+        t = T64.ref();
+        a = A64.ref();
+        c = C64.ref();
+    }
+    auto P = params<double>(1);
+    P.sys_base = slot;
+    P.in = X.ref();
+    P.out = t;
+    { auto pb_ = prof_begin(pcls_rel[0], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_f64(P, Epi::MINV, 1, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+    P.p_out = 0;
+    P.in = t;
+    P.z = X.ref();
+    P.out = a;
+    { auto pb_ = prof_begin(pcls_rel[1], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_f64(P, Epi::SCHUR_MDINV, 1, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+    P.p_out = 1;
+    P.in = a;
+    P.z = FieldRef{};
+    P.out = c;
+    { auto pb_ = prof_begin(pcls_rel[2], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_f64(P, Epi::D_MINVDAG, 1, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+    P.p_out = 0;
+    P.in = c;
+    P.z = a;
+    P.b = B64.ref();
+    P.out = R.ref();
+    { auto pb_ = prof_begin(pcls_rel[3], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_f64(P, Epi::D_NORMAL_RESID, 1, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+    return ODWF_OK;
+}
+
+int BatchCG::service(cudaStream_t s) {
+    const size_t n5 = E->sites5();
+    for (int i = 0; i < cap; ++i) {
+        if (!active[i] || st_host[i].status != kNeedUpdate) continue;
+        if (mixed)  // X64 += x_in, x_in = 0
+            ODWF_CK(launch_vec(Sp::F32, Sp::F64, Xin.ref(), X64.ref(), n5, E->ns, 2, 0.0, st, 0, 0, nullptr, nullptr,
+                               i, 1, s));
+        int rc = fp64_residual(i, X64, R64, s);
+        if (rc) return rc;
+        ODWF_CK(launch_state(st + i, 1, 1, tol * tol, s));
+        if (mixed) {
+            ODWF_CK(launch_vec(Sp::F64, Sp::F32, R64.ref(), Rin.ref(), n5, E->ns, 0, 0.0, st, 1, kRunning, nullptr,
+                               nullptr, i, 1, s));
+            ODWF_CK(launch_vec(Sp::F32, low, Rin.ref(), Pl.ref(), n5, E->ns, 1, 0.0, st, 1, kRunning, nullptr, nullptr,
+                               i, 1, s));
+        } else {
+            ODWF_CK(launch_vec(Sp::F64, Sp::F64, R64.ref(), P64.ref(), n5, E->ns, 1, 0.0, st, 1, kRunning, nullptr,
+                               nullptr, i, 1, s));
+        }
+        n_reliable[i] += 1;
+        st_host[i].status = kRunning;  // host view until the next poll
+    }
+    return ODWF_OK;
+}
+
+int BatchCG::finalize(int slot, double2* x_ext, cudaStream_t s, double* true_resid) {
+    ODWF_CK(cudaMemcpyAsync(st_host + slot, st + slot, sizeof(SysState), cudaMemcpyDeviceToHost, s));
+    ODWF_CK(cudaStreamSynchronize(s));
+    const int stt = st_host[slot].status;
+    if (stt != kDone && stt != kMaxIter) {
+        // breakdown (or an unfinished slot): fold and recompute the true residual
+        if (mixed)
+            ODWF_CK(launch_vec(Sp::F32, Sp::F64, Xin.ref(), X64.ref(), E->sites5(), E->ns, 2, 0.0, st, 0, 0, nullptr,
+                               nullptr, slot, 1, s));
+        int rc = fp64_residual(slot, X64, R64, s);
+        if (rc) return rc;
+    }
+    if (x_ext) ODWF_CK(launch_unpack(Sp::F64, X64.ref_sys(slot), x_ext, E->g, 0, E->ns, 1, s));
+    ODWF_CK(cudaMemcpyAsync(st_host + slot, st + slot, sizeof(SysState), cudaMemcpyDeviceToHost, s));
+    ODWF_CK(cudaStreamSynchronize(s));
+    const SysState& S = st_host[slot];
+    if (true_resid) *true_resid = S.bb > 0 ? std::sqrt(S.sum / S.bb) : 0.0;
+    return ODWF_OK;
+}
+
+}  // namespace odwf

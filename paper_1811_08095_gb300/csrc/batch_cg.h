@@ -1,0 +1,78 @@
+// Slot-based batched CG on the even-odd Schur normal equations S^dag S x = b.
+//
+// Every iteration is four fused hop launches plus one vector update, each covering all
+// slots of the batch (grid.y = slot); a slot whose status is not "running" exits at its
+// first instruction, so converged systems cost nothing and new systems can be admitted
+// into free slots between iterations (continuous batching).
+//   K1  t = M^-1 H_oe p
+//   K2  a = M^-dag (p - M^-1 H_eo t),   |p - M^-1 H_eo t|^2 = p^dag S^dag S p  -> alpha
+//   K3  c = M^-dag H_eo^dag a
+//   K4  A p = M^dag a - H_oe^dag c;  r -= alpha A p;  x += alpha p;  |r|^2 -> beta, status
+//   P   p = r + beta p
+// Mixed precision: p, t, a, c are stored in FP16 / BF16 (per-site scale) or FP32, r and x
+// in FP32, all arithmetic FP32.  A system whose inner residual falls below delta times its
+// largest value since the last update (or below the target) is parked; the host then
+// folds x into the FP64 solution, recomputes r = b - S^dag S x in FP64 on the GPU and
+// restarts the inner iteration from it (reliable updates).
+#pragma once
+
+#include <chrono>
+#include <vector>
+
+#include "engine.h"
+#include "profile.h"
+
+namespace odwf {
+
+struct BatchCG {
+    Engine* E = nullptr;
+    int cap = 0;
+    bool mixed = false;
+    Sp low = Sp::F16;
+    Lk lk = Lk::F12;
+    double delta = 0.1;
+    double tol = 1e-10;
+    int max_iter = 10000;
+
+    // per-slot fields (slabs of `cap`)
+    HalfField X64, R64, B64;       // FP64 solution, residual, right-hand side
+    HalfField P64, T64, A64, C64;  // FP64 CG (mixed = false) operator fields
+    HalfField Rin, Xin;            // mixed: FP32 inner residual / solution
+    HalfField Pl, Tl, Al, Cl;      // mixed: low-precision operator fields
+    HalfField T1, A1, C1;          // mixed: FP64 temporaries for reliable updates (one system)
+
+    SysState* st = nullptr;        // device [cap]
+    SysState* st_host = nullptr;   // pinned mirror
+    double* r_dev = nullptr;       // device [cap]
+    double* partials = nullptr;    // device [cap * nblk]
+    unsigned* counters = nullptr;  // device [cap]
+    std::vector<int> n_reliable;
+    std::vector<int> active;       // host view: slot holds a system
+    std::vector<double> mq;
+    std::vector<double> slot_tol;
+    int pcls[5] = {-1, -1, -1, -1, -1};  // profiler classes: K1..K4, p update
+    int pcls_rel[4] = {-1, -1, -1, -1};  // FP64 residual hops of the reliable update
+
+    ~BatchCG();
+    int init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStream_t s);
+    // b_ext: device pointer to an even-site external field (complex128)
+    // tol_slot / max_iter_slot <= 0 keep the batch defaults
+    int admit(int slot, const double2* b_ext, double mq_slot, cudaStream_t s, double tol_slot = 0,
+              int max_iter_slot = 0);
+    int admit_internal(int slot, cudaStream_t s, double tol_slot = 0, int max_iter_slot = 0);  // B64[slot] filled
+    int release(int slot);  // slot free for the next admit
+    int run_iterations(int k, cudaStream_t s);
+    int poll(cudaStream_t s);                      // refresh st_host (synchronizes s)
+    int service(cudaStream_t s);                   // reliable updates for parked slots
+    int finalize(int slot, double2* x_ext, cudaStream_t s, double* true_resid);
+    bool slot_running(int i) const;
+    bool slot_finished(int i) const;
+    int any_running() const;
+
+   private:
+    template <class R>
+    HopParams<R> params(int p_out) const;
+    int fp64_residual(int slot, const HalfField& X, const HalfField& R, cudaStream_t s);
+};
+
+}  // namespace odwf

@@ -1,0 +1,108 @@
+// Host engine behind the C ABI: one handle per (lattice, Ns, m0, weights).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/odwf.h"
+#include "kernels.cuh"
+#include "kernels.h"
+
+namespace odwf {
+
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define ODWF_CK(call)                                           \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+    } while (0)
+
+bool is_device_ptr(const void* p);
+
+// A device buffer owned by the engine.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// A half field for `nsys` systems (system slabs `stride` bytes apart) in format `sp`.
+struct HalfField {
+    Sp sp = Sp::F64;
+    void* data = nullptr;
+    float* norm = nullptr;
+    size_t stride = 0;       // bytes per system
+    size_t norm_stride = 0;  // floats per system
+    FieldRef ref() const { return FieldRef{data, norm, stride, norm_stride}; }
+    FieldRef ref_shared() const { return FieldRef{data, norm, 0, 0}; }  // same buffer for every system
+    FieldRef ref_sys(int i) const {  // system i as a single-system field
+        return FieldRef{(char*)data + i * stride, norm ? norm + i * norm_stride : nullptr, 0, 0};
+    }
+};
+
+struct Engine {
+    odwf_lattice lat{};
+    Geom g{};
+    int ns = 0;
+    int lg_ns = 0;
+    double m0 = 0, mq = 0;
+    std::vector<double> omega;
+    Coef5<double> cf64{};
+    Coef5<float> cf32{};
+    int device = 0;
+
+    // packed links
+    void* links_d18 = nullptr;
+    void* links_f18 = nullptr;
+    void* links_f12 = nullptr;
+    bool gauge_set = false;
+
+    // named workspaces (grow-only)
+    std::map<std::string, DevBuf> ws;
+    void* pinned = nullptr;
+    size_t pinned_bytes = 0;
+
+    ~Engine();
+    int init(const odwf_lattice* l, int Ns, double m0_, double mq_, const double* w);
+    int set_gauge(const void* U, cudaStream_t st);
+
+    size_t vh() const { return (size_t)g.Vh; }
+    size_t sites5() const { return (size_t)g.Vh * ns; }
+    size_t half_bytes(Sp sp) const;
+    size_t norm_count() const { return sites5(); }
+    size_t ext_bytes(int mode) const { return (mode == ODWF_MODE_FULL ? 2 : 1) * sites5() * 192; }
+
+    void* get_ws(const std::string& name, size_t bytes, int* rc);
+    int alloc_half(const std::string& name, Sp sp, int nsys, HalfField* f);
+    void* host_stage(size_t bytes, int* rc);
+
+    // parameters of one hop launch
+    template <class R>
+    HopParams<R> hop_params(int p_out, const double* r_dev) const;
+
+    // FP64 operators on internal half fields (single system, r from r_dev[0])
+    int apply_schur64(const HalfField& in, const HalfField& out, bool dag, const double* r_dev, cudaStream_t st);
+    int apply_full64(const HalfField& in_e, const HalfField& in_o, const HalfField& out_e, const HalfField& out_o,
+                     bool dag, const double* r_dev, cudaStream_t st);
+
+    // C-ABI level operations
+    int apply(void* out, const void* in, int mode, bool dag, cudaStream_t st);
+    int apply_normal(void* out, const void* in, int system, cudaStream_t st);
+    int apply_m5(void* out, const void* in, long n_sites, int op, cudaStream_t st);
+    int apply_low_normal(void* out, const void* in, int prec, int recon, cudaStream_t st);
+    int solve(int nsys, void* const* x, const void* const* b, const double* mq_arr, const odwf_solve_params* prm,
+              odwf_solve_stats* stats, cudaStream_t st);
+    int solve_full(void* x, const void* b, const odwf_solve_params* prm, odwf_solve_stats* stats,
+                   cudaStream_t st);
+};
+
+}  // namespace odwf
+
+struct odwf_handle {
+    odwf::Engine e;
+};

@@ -1,0 +1,76 @@
+// Host-side launchers of the ODWF kernels (definitions in kernels_f64.cu, kernels_mixed.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "odwf_internal.h"
+
+namespace odwf {
+
+enum class Sp { F64 = 0, F32 = 1, F16 = 2, BF16 = 3 };
+enum class Lk { D18 = 0, F18 = 1, F12 = 2 };
+
+struct FieldRef;
+template <class R>
+struct HopParams;
+
+// Named epilogues (see kernels.cuh)
+enum class Epi {
+    MINV,                 // M^-1 H p
+    SCHUR,                // z - M^-1 H t
+    SCHUR_NORM_MDINV,     // M^-dag (z - M^-1 H t), |z - M^-1 H t|^2 -> alpha
+    SCHUR_MDINV,          // M^-dag (z - M^-1 H t)
+    FULL,                 // M z + H p
+    PLAIN,                // H p
+    ZMINUS_POSTMINV,      // M^-1 (z - H p)
+    ZMINUS,               // z - H p
+    D_MINVDAG,            // M^-dag H^dag a
+    D_NORMAL,             // M^dag z - H^dag c
+    D_NORMAL_CG,          // fused CG update (r, x, |r|^2 -> beta)
+    D_NORMAL_RESID,       // b - (M^dag z - H^dag c), |.|^2 -> sum
+    D_ZMINUS,             // z - H^dag c
+    D_FULL,               // M^dag z + H^dag p
+    D_PLAIN,              // H^dag p
+    D_SCHUR2,             // z - M^-dag H^dag t
+    D_ZMINUS_POSTMINVDAG, // M^-dag (z - H^dag p)
+};
+
+// FP64 path (double spinors, 18-real double links, FP64 arithmetic)
+cudaError_t launch_hop_f64(const HopParams<double>& P, Epi e, int nsys, cudaStream_t st);
+// Mixed path (low-precision operator fields, FP32 accumulators r/x, float links, FP32 arithmetic)
+cudaError_t launch_hop_mixed(const HopParams<float>& P, Epi e, Sp low, Lk lk, int nsys, cudaStream_t st);
+
+// Site-local M, M^dag, M^-1, M^-dag (op 0..3)
+cudaError_t launch_m5_f64(const FieldRef& in, const FieldRef& out, size_t n_sites, int ns, const double* r_sys,
+                          int sys_base, int nsys, int op, const Coef5<double>& cf, cudaStream_t st);
+cudaError_t launch_m5_mixed(Sp low, const FieldRef& in, const FieldRef& out, size_t n_sites, int ns,
+                            const double* r_sys, int sys_base, int nsys, int op, const Coef5<float>& cf,
+                            cudaStream_t st);
+
+// Layout conversion between external complex128 fields and internal half fields
+cudaError_t launch_pack(Sp sp, const double2* ext, const FieldRef& out, const Geom& g, int p, int ns, int ext_mode,
+                        cudaStream_t st);
+cudaError_t launch_unpack(Sp sp, const FieldRef& in, double2* ext, const Geom& g, int p, int ns, int ext_mode,
+                          cudaStream_t st);
+
+// Vector kernels (kinds as in kernels.cuh); x and y formats given separately
+cudaError_t launch_vec(Sp spx, Sp spy, const FieldRef& x, const FieldRef& y, size_t n5, int ns, int kind,
+                       double coef, SysState* st, int gate, int need, double* partials,
+                       unsigned* counters, int sys_base, int nsys, cudaStream_t stream);
+
+// profiling counter for the next launch_vec (nullptr: none); single-threaded use per call site
+void set_vec_prof(unsigned long long* c);
+
+cudaError_t launch_state(SysState* st, int nsys, int mode, double tol2, cudaStream_t stream);
+
+// Gauge packing from external complex128 U[mu][t][z][y][x][3][3] (device)
+cudaError_t launch_pack_links(const double2* U, void* d18, void* f18, void* f12, const Geom& g, cudaStream_t st);
+
+int lg2(int v);
+
+// process-wide count of kernel launches issued by the library
+void note_launch();
+long long launch_count();
+inline int blocks_for(size_t n, int bs) { return (int)((n + bs - 1) / bs); }
+
+}  // namespace odwf

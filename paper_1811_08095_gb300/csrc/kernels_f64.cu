@@ -1,0 +1,211 @@
+// FP64 kernels, layout conversion, vector and gauge-packing kernels.
+#include "kernels.cuh"
+#include "kernels.h"
+
+#include <atomic>
+
+namespace odwf {
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+int lg2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+namespace {
+constexpr int kBS = 256;
+
+template <int F>
+cudaError_t hop64(const HopParams<double>& P, int nsys, cudaStream_t st) {
+    const size_t n = (size_t)P.g.Vh * P.ns;
+    dim3 grid(blocks_for(n, kBS), nsys);
+    note_launch(); hop_kernel<SpF64, SpF64, SpF64, SpF64, LinkD18, double, F><<<grid, kBS, 0, st>>>(P);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_hop_f64(const HopParams<double>& P, Epi e, int nsys, cudaStream_t st) {
+    switch (e) {
+        case Epi::MINV: return hop64<EPI_MINV>(P, nsys, st);
+        case Epi::SCHUR: return hop64<EPI_SCHUR>(P, nsys, st);
+        case Epi::SCHUR_NORM_MDINV: return hop64<EPI_SCHUR_NORM_MDINV>(P, nsys, st);
+        case Epi::SCHUR_MDINV: return hop64<EPI_SCHUR_NORM_MDINV_STORE>(P, nsys, st);
+        case Epi::FULL: return hop64<EPI_FULL>(P, nsys, st);
+        case Epi::PLAIN: return hop64<EPI_PLAIN>(P, nsys, st);
+        case Epi::ZMINUS_POSTMINV: return hop64<EPI_ZMINUS_POSTMINV>(P, nsys, st);
+        case Epi::ZMINUS: return hop64<EPI_ZMINUS>(P, nsys, st);
+        case Epi::D_MINVDAG: return hop64<EPID_MINVDAG>(P, nsys, st);
+        case Epi::D_NORMAL: return hop64<EPID_NORMAL>(P, nsys, st);
+        case Epi::D_NORMAL_CG: return hop64<EPID_NORMAL_CG>(P, nsys, st);
+        case Epi::D_NORMAL_RESID: return hop64<EPID_NORMAL_RESID>(P, nsys, st);
+        case Epi::D_ZMINUS: return hop64<EPID_ZMINUS>(P, nsys, st);
+        case Epi::D_FULL: return hop64<EPID_FULL>(P, nsys, st);
+        case Epi::D_PLAIN: return hop64<EPID_PLAIN>(P, nsys, st);
+        case Epi::D_SCHUR2: return hop64<EPID_SCHUR2>(P, nsys, st);
+        case Epi::D_ZMINUS_POSTMINVDAG: return hop64<EPID_ZMINUS_POSTMINVDAG>(P, nsys, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_m5_f64(const FieldRef& in, const FieldRef& out, size_t n_sites, int ns, const double* r_sys,
+                          int sys_base, int nsys, int op, const Coef5<double>& cf, cudaStream_t st) {
+    dim3 grid(blocks_for(n_sites * ns, kBS), nsys);
+    note_launch(); m5_kernel<SpF64, SpF64, double><<<grid, kBS, 0, st>>>(in, out, n_sites, ns, lg2(ns), r_sys, sys_base, op, cf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(Sp sp, const double2* ext, const FieldRef& out, const Geom& g, int p, int ns, int ext_mode,
+                        cudaStream_t st) {
+    const int grid = blocks_for((size_t)g.Vh * ns, kBS);
+    const int lg = lg2(ns);
+    switch (sp) {
+        case Sp::F64: note_launch(); pack_kernel<SpF64><<<grid, kBS, 0, st>>>(ext, out, g, p, ns, lg, ext_mode); break;
+        case Sp::F32: note_launch(); pack_kernel<SpF32><<<grid, kBS, 0, st>>>(ext, out, g, p, ns, lg, ext_mode); break;
+        case Sp::F16: note_launch(); pack_kernel<SpF16><<<grid, kBS, 0, st>>>(ext, out, g, p, ns, lg, ext_mode); break;
+        case Sp::BF16: note_launch(); pack_kernel<SpBF16><<<grid, kBS, 0, st>>>(ext, out, g, p, ns, lg, ext_mode); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(Sp sp, const FieldRef& in, double2* ext, const Geom& g, int p, int ns, int ext_mode,
+                          cudaStream_t st) {
+    const int grid = blocks_for((size_t)g.Vh * ns, kBS);
+    const int lg = lg2(ns);
+    switch (sp) {
+        case Sp::F64: note_launch(); unpack_kernel<SpF64><<<grid, kBS, 0, st>>>(in, ext, g, p, ns, lg, ext_mode); break;
+        case Sp::F32: note_launch(); unpack_kernel<SpF32><<<grid, kBS, 0, st>>>(in, ext, g, p, ns, lg, ext_mode); break;
+        case Sp::F16: note_launch(); unpack_kernel<SpF16><<<grid, kBS, 0, st>>>(in, ext, g, p, ns, lg, ext_mode); break;
+        case Sp::BF16: note_launch(); unpack_kernel<SpBF16><<<grid, kBS, 0, st>>>(in, ext, g, p, ns, lg, ext_mode); break;
+    }
+    return cudaGetLastError();
+}
+
+thread_local unsigned long long* g_vec_prof = nullptr;  // counter for the next vec launch (profiling)
+
+void set_vec_prof(unsigned long long* c) { g_vec_prof = c; }
+
+namespace {
+template <class SX, class SY, class R>
+cudaError_t vec_t(const FieldRef& x, const FieldRef& y, size_t n5, int ns, int kind, double coef, SysState* st,
+                  int gate, int need, double* partials, unsigned* counters, int sys_base, int nsys,
+                  cudaStream_t stream) {
+    dim3 grid(blocks_for(n5, kBS), nsys);
+    note_launch(); vec_kernel<SX, SY, R><<<grid, kBS, 0, stream>>>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters,
+                                                    sys_base, g_vec_prof);
+    return cudaGetLastError();
+}
+
+template <class SX>
+cudaError_t vec_y(Sp spy, const FieldRef& x, const FieldRef& y, size_t n5, int ns, int kind, double coef,
+                  SysState* st, int gate, int need, double* partials, unsigned* counters, int sys_base,
+                  int nsys, cudaStream_t stream) {
+    const bool dx = std::is_same<SX, SpF64>::value;
+    switch (spy) {
+        case Sp::F64:
+            return vec_t<SX, SpF64, double>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base,
+                                            nsys, stream);
+        case Sp::F32:
+            if (dx) return vec_t<SX, SpF32, double>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
+            return vec_t<SX, SpF32, float>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base,
+                                           nsys, stream);
+        case Sp::F16:
+            if (dx) return vec_t<SX, SpF16, double>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
+            return vec_t<SX, SpF16, float>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base,
+                                           nsys, stream);
+        case Sp::BF16:
+            if (dx) return vec_t<SX, SpBF16, double>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
+            return vec_t<SX, SpBF16, float>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters,
+                                            sys_base, nsys, stream);
+    }
+    return cudaErrorInvalidValue;
+}
+}  // namespace
+
+cudaError_t launch_vec(Sp spx, Sp spy, const FieldRef& x, const FieldRef& y, size_t n5, int ns, int kind,
+                       double coef, SysState* st, int gate, int need, double* partials,
+                       unsigned* counters, int sys_base, int nsys, cudaStream_t stream) {
+    switch (spx) {
+        case Sp::F64: return vec_y<SpF64>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
+        case Sp::F32: return vec_y<SpF32>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
+        case Sp::F16: return vec_y<SpF16>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
+        case Sp::BF16: return vec_y<SpBF16>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// One thread per system: CG bookkeeping between phases.
+//   mode 0 (init):  rr = bb = sum, r_max = sqrt(sum), status running (done when b = 0)
+//   mode 1 (after a reliable update, sum = ||b - A x||^2): done / max-iter / restart with
+//                   beta = sum / rr_prev, rr = sum, r_max = sqrt(sum)
+__global__ void state_kernel(SysState* st, int nsys, int mode, double tol2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nsys) return;
+    SysState& S = st[i];
+    if (mode == 0) {
+        S.bb = S.sum;
+        S.rr = S.sum;
+        S.stop_rr = tol2 * S.sum;
+        S.r_max = sqrt(S.sum);
+        S.iter = 0;
+        S.alpha = S.beta = 0.0;
+        S.status = (S.sum > 0.0) ? kRunning : kDone;
+    } else {
+        if (S.status != kNeedUpdate) return;
+        const double rt = S.sum;
+        if (!isfinite(rt)) {
+            S.status = kBreakdown;
+        } else if (rt <= S.stop_rr) {
+            S.rr = rt;
+            S.status = kDone;
+        } else if (S.iter >= S.max_iter) {
+            S.rr = rt;
+            S.status = kMaxIter;
+        } else {
+            S.beta = rt / S.rr;
+            S.rr = rt;
+            S.r_max = sqrt(rt);
+            S.status = kRunning;
+        }
+    }
+}
+
+
+cudaError_t launch_state(SysState* st, int nsys, int mode, double tol2, cudaStream_t stream) {
+    note_launch(); state_kernel<<<blocks_for(nsys, 128), 128, 0, stream>>>(st, nsys, mode, tol2);
+    return cudaGetLastError();
+}
+
+// One thread per (parity, mu, half-site): U_mu(x) -> packed formats
+__global__ void pack_links_kernel(const double2* __restrict__ U, double* d18, float* f18, float* f12, Geom g) {
+    const size_t gi = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nh = (size_t)g.Vh;
+    if (gi >= 8 * nh) return;
+    const int h = (int)(gi % nh);
+    const int mu = (int)((gi / nh) % 4);
+    const int p = (int)(gi / (4 * nh));
+    int c[4];
+    site_coords(g, p, h, c);
+    const size_t V = 2 * nh;
+    const size_t lex = (size_t)c[0] + (size_t)g.L[0] * (c[1] + (size_t)g.L[1] * (c[2] + (size_t)g.L[2] * c[3]));
+    const double2* src = U + ((size_t)mu * V + lex) * 9;
+    const size_t o = ((size_t)(p * 4 + mu) * nh + h);
+    for (int k = 0; k < 9; ++k) {
+        const double2 q = src[k];
+        if (d18) { d18[o * 18 + 2 * k] = q.x; d18[o * 18 + 2 * k + 1] = q.y; }
+        if (f18) { f18[o * 20 + 2 * k] = (float)q.x; f18[o * 20 + 2 * k + 1] = (float)q.y; }
+        if (f12 && k < 6) { f12[o * 12 + 2 * k] = (float)q.x; f12[o * 12 + 2 * k + 1] = (float)q.y; }
+    }
+    if (f18) { f18[o * 20 + 18] = 0.f; f18[o * 20 + 19] = 0.f; }
+}
+
+cudaError_t launch_pack_links(const double2* U, void* d18, void* f18, void* f12, const Geom& g, cudaStream_t st) {
+    const size_t n = 8 * (size_t)g.Vh;
+    note_launch(); pack_links_kernel<<<blocks_for(n, 256), 256, 0, st>>>(U, (double*)d18, (float*)f18, (float*)f12, g);
+    return cudaGetLastError();
+}
+
+}  // namespace odwf

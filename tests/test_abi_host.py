@@ -1,0 +1,90 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every entry point that
+include/odwf.h declares, and its host-only logic (the optimal-weight generator and
+argument validation) agrees with the oracle.  No GPU compute is called here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1811_08095_gb300 as odwf
+from oracle import zolotarev
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return odwf.load(build_if_missing=True)
+
+
+def declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(inc, fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w[\w\s\*]*?\b((?:odwf|serve)_\w+)\s*\(", txt, flags=re.M))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), "libodwf.so does not export %s" % n
+
+
+def test_library_is_in_tree(lib):
+    assert os.path.dirname(odwf.lib_path()).startswith(ROOT)
+
+
+@pytest.mark.parametrize("ns", [2, 4, 8, 16])
+@pytest.mark.parametrize("variant,shifted", [(odwf.ODWF_OMEGA_SHIFTED_R5, True), (odwf.ODWF_OMEGA_PLAIN, False)])
+def test_omega_matches_oracle(lib, ns, variant, shifted):
+    for lmin, lmax in [(0.05, 6.0), (0.05, 6.2), (0.1, 2.5)]:
+        w, dz = odwf.odwf_zolotarev_omega(ns, lmin, lmax, variant)
+        wo, dzo = zolotarev.omega(ns, lmin, lmax, shifted)
+        # the oracle finds the weights numerically; its accuracy falls with Ns (flat maxima)
+        assert np.abs(w / wo - 1).max() < 1e-7
+        assert abs(dz / dzo - 1) < 1e-6
+
+
+@pytest.mark.parametrize("ns", [16, 32])
+def test_omega_shifted_bound_large_ns(lib, ns):
+    """Sec. 2: 0 <= 1 - S(lambda) <= 2 d_Z with R5-symmetric weights, checked directly."""
+    lmin, lmax = 0.05, 6.2
+    w, dz = odwf.odwf_zolotarev_omega(ns, lmin, lmax, odwf.ODWF_OMEGA_SHIFTED_R5)
+    assert np.array_equal(w, w[::-1])
+    lam = np.geomspace(lmin, lmax, 100001)
+    T = np.ones_like(lam)
+    for ws in w:
+        T *= (1 - ws * lam) / (1 + ws * lam)
+    one_minus_s = 1 - (1 - T) / (1 + T)
+    assert one_minus_s.min() > -1e-12
+    assert one_minus_s.max() <= 2 * dz * (1 + 1e-3) + 1e-14
+
+
+def test_omega_invalid_arguments(lib):
+    out = np.zeros(8)
+    dz = ctypes.c_double()
+    for args in [(7, 0.05, 6.0, 0), (0, 0.05, 6.0, 0), (8, 0.0, 6.0, 0), (8, 6.0, 0.05, 0), (8, 0.05, 6.0, 9)]:
+        rc = lib.odwf_zolotarev_omega(args[0], args[1], args[2], args[3],
+                                      out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(dz))
+        assert rc == odwf._lib.ODWF_EINVAL
+        assert lib.odwf_last_error()
+
+
+def test_create_rejects_bad_sizes(lib):
+    om = np.ones(8)
+    h = ctypes.c_void_p()
+    for dims, ns in [((3, 4, 4, 4), 8), ((4, 4, 4, 0), 8), ((4, 4, 4, 4), 6), ((4, 4, 4, 4), 64)]:
+        lat = odwf._lib.odwf_lattice()
+        for i in range(4):
+            lat.dims[i] = dims[i]
+        lat.t_antiperiodic = 1
+        rc = lib.odwf_create(ctypes.byref(lat), ns, 1.3, 0.01, om.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h))
+        assert rc == odwf._lib.ODWF_EINVAL, dims
+    assert lib.odwf_create(None, 8, 1.3, 0.01, None, ctypes.byref(h)) == odwf._lib.ODWF_EINVAL
