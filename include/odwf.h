@@ -179,6 +179,34 @@ int odwf_apply_normal_prec(odwf_handle* h, void* out, const void* in, int prec, 
 int odwf_apply_m5(odwf_handle* h, void* out, const void* in, long n_sites, int op, void* stream);
 
 /*
+ * odwf_apply_m5 without any device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that must not let a library call cudaMalloc -- applications
+ * whose own memory manager has already reserved the GPU's memory (a library-side
+ * cudaMalloc would fail or fragment that pool) and latency-critical code that cannot
+ * accept the device-wide synchronisation cudaMalloc and cudaFree imply.
+ *
+ * Computes out = op(in) for op 0 = M, 1 = M^dag, 2 = M^-1, 3 = M^-dag exactly as
+ * odwf_apply_m5 does, for the operator with Ns, m0, mq and weights omega (host array of
+ * Ns doubles; rho = sigma = omega), on n_sites sites in the layout
+ * [s][site][spin][colour] (complex128).  No handle is needed.
+ *   in, out   device memory, n_sites * Ns * 12 complex values each, not overlapping;
+ *             host pointers are rejected with ODWF_EINVAL (staging them would allocate).
+ *   limit     n_sites * Ns <= 65536; larger requests return ODWF_EINVAL.  The staging
+ *             fields live in a fixed 24 MiB + 256 B device array that every GPU which
+ *             loads the library keeps until the process exits.
+ *   set-up    the first call on each device looks up that array's device address
+ *             (cudaGetSymbolAddress) with the device current; make that first call
+ *             before any stream capture begins.
+ *   sharing   every call uses the same array, which keeps the last call's contents
+ *             (each call writes all it reads first); calls whose work overlaps on the
+ *             GPU -- different streams, or host threads -- race on it and must be
+ *             serialised by the caller.
+ * Stream-ordered on `stream`; returns ODWF_OK, ODWF_EINVAL or ODWF_ECUDA.
+ */
+int odwf_apply_m5_noalloc(int Ns, double m0, double mq, const double* omega, void* out, const void* in,
+                          long n_sites, int op, void* stream);
+
+/*
  * Solve one system by conjugate gradient (Sec. 2).  x: initial guess ignored, result
  * written; b: right-hand side (layouts by system).  stats may be NULL.
  * Returns ODWF_OK on convergence to params->tol, ODWF_ENOCONV at max_iter (x holds the

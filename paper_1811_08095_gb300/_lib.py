@@ -85,6 +85,7 @@ _SIGS = {
     "odwf_apply_normal": ([P, P, P, I, P], I),
     "odwf_apply_normal_prec": ([P, P, P, I, I, P], I),
     "odwf_apply_m5": ([P, P, P, ctypes.c_long, I, P], I),
+    "odwf_apply_m5_noalloc": ([I, D, D, P, P, P, ctypes.c_long, I, P], I),
     "odwf_cg_solve": ([P, P, P, ctypes.POINTER(odwf_solve_params), P, P], I),
     "odwf_cg_solve_batched": ([P, I, P, P, P, ctypes.POINTER(odwf_solve_params), P, P], I),
     "odwf_profile_enable": ([I], I),
