@@ -145,6 +145,21 @@ def ncu_traffic(kernel_class):
     return None
 
 
+def aggregate(t_local_s: float, solves_local: int, dist=None, device=None):
+    """Whole-job throughput of independent replicas: every rank's solves over the slowest rank's
+    timed region (max over ranks), as the replicas-only multi-GPU contract asks."""
+    if dist is None:
+        return solves_local / t_local_s, t_local_s, solves_local
+    import torch
+
+    t = torch.tensor([t_local_s, float(solves_local)], dtype=torch.float64, device=device)
+    tmax = t[:1].clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    n = t[1:].clone()
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(n.item()) / float(tmax.item()), float(tmax.item()), int(n.item())
+
+
 def read_profile(lib):
     import ctypes
 
@@ -189,7 +204,8 @@ def run_ours(args, world, rank, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step(prec):
-        return h.cg_solve_batched(xs, bs, list(MASSES), tol=TOL, max_iter=200000, prec=prec, stream=stream)
+        return h.cg_solve_batched(xs, bs, list(MASSES), tol=TOL, max_iter=200000, prec=prec, delta=args.delta,
+                                  link_recon=args.link_recon, stream=stream)
 
     for _ in range(args.warmup):
         stats = step(args.prec)
@@ -225,13 +241,7 @@ def run_ours(args, world, rank, local):
     prof = read_profile(lib)
     lib.odwf_profile_enable(0)
 
-    t_total = sum(step_ms) / 1e3
-    if dist:
-        tt = torch.tensor([t_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
-    nsolves = len(MASSES) * args.steps * world
-    value = nsolves / t_total
+    value, t_total, nsolves = aggregate(sum(step_ms) / 1e3, len(MASSES) * args.steps, dist, dev)
     for st in all_stats:
         for s in st:
             assert s["status"] == 0 and s["true_resid"] <= TOL, s
@@ -262,12 +272,13 @@ def run_ours(args, world, rank, local):
     h2d = sum(b.numel() * b.element_size() for b in bh)
     d2h = sum(x.numel() * x.element_size() for x in xh)
     h.cg_solve_batched([x.numpy() for x in xh], [b.numpy() for b in bh], list(MASSES), tol=TOL, max_iter=200000,
-                       prec=args.prec, stream=stream)  # warm
+                       prec=args.prec, delta=args.delta, link_recon=args.link_recon, stream=stream)  # warm
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         h.cg_solve_batched([x.numpy() for x in xh], [b.numpy() for b in bh], list(MASSES), tol=TOL,
-                           max_iter=200000, prec=args.prec, stream=stream)
+                           max_iter=200000, prec=args.prec, delta=args.delta, link_recon=args.link_recon,
+                           stream=stream)
     e2e_s = time.perf_counter() - t0
     e2e = {"value": round(len(MASSES) * args.steps * world / e2e_s, 4), "unit": "solves/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
@@ -312,8 +323,9 @@ def run_ours(args, world, rank, local):
                        "rhs": "one unit-Gaussian right-hand side per mass (seeds 100-102)",
                        "gauge": "U = exp(0.25 i H), H Gaussian traceless Hermitian (seed 2)",
                        "omega": "shifted (R5) Zolotarev on [0.05, 6.2]", "tol": TOL,
-                       "precision": "%s storage (per-site FP32 scale), FP32 links (12 reals), FP32 arithmetic, "
-                                    "FP64 reliable updates and reductions" % args.prec,
+                       "precision": "%s storage (per-site FP32 scale), FP32 links (%d reals), FP32 arithmetic, "
+                                    "FP64 reliable updates (delta %g) and reductions" % (args.prec, args.link_recon,
+                                                                                        args.delta),
                        "solver": "batched even-odd CG on S^dag S, 3 systems per launch",
                        "l2": "flushed between steps (512 MB write); per-system working set > 1 GB",
                        "parallelism": "replicas only" if world > 1 else "single GPU",
@@ -369,6 +381,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="f16", choices=["f16", "bf16", "f32"])
+    ap.add_argument("--delta", type=float, default=0.01, help="reliable-update threshold")
+    ap.add_argument("--link-recon", type=int, default=12, choices=[12, 18])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     args = ap.parse_args()

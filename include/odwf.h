@@ -89,7 +89,7 @@ typedef struct {
                            storage for the inner operator fields, FP32 arithmetic, FP64 reliable updates */
     double delta;       /* reliable-update trigger: recompute the FP64 residual when the inner
                            residual drops below delta x its largest value since the last update
-                           (<= 0 selects 0.1) */
+                           (<= 0 selects 0.01) */
     int32_t system;     /* ODWF_SYS_* */
     int32_t link_recon; /* mixed inner links: 12 (two rows, third reconstructed) or 18; 0 = 12 */
     double mq;          /* quark mass for this solve; NaN keeps the handle's m_q */

@@ -132,7 +132,7 @@ class Handle:
         check(self._lib.odwf_apply_m5(self._h, ptr(out), ptr(inp), int(n_sites), int(op), stream_ptr(stream)))
         return out
 
-    def cg_solve(self, x, b, tol=1e-10, max_iter=100000, prec="f64", delta=0.1, system=ODWF_SYS_SCHUR_NORMAL,
+    def cg_solve(self, x, b, tol=1e-10, max_iter=100000, prec="f64", delta=0.01, system=ODWF_SYS_SCHUR_NORMAL,
                  link_recon=12, mq=None, check_every=8, stream=None, raise_on_error=True):
         p = _params(tol, max_iter, prec, delta, system, link_recon, mq, check_every)
         st = _lib.odwf_solve_stats()
@@ -143,7 +143,7 @@ class Handle:
         d["rc"] = rc
         return d
 
-    def cg_solve_batched(self, xs, bs, mqs=None, tol=1e-10, max_iter=100000, prec="f64", delta=0.1,
+    def cg_solve_batched(self, xs, bs, mqs=None, tol=1e-10, max_iter=100000, prec="f64", delta=0.01,
                          link_recon=12, check_every=8, stream=None, raise_on_error=True):
         n = len(xs)
         assert len(bs) == n

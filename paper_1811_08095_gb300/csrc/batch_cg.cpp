@@ -35,7 +35,7 @@ int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStr
     mixed = prm.prec != ODWF_F64;
     low = (Sp)prm.prec;
     lk = prm.link_recon == 18 ? Lk::F18 : Lk::F12;
-    delta = prm.delta > 0 ? prm.delta : 0.1;
+    delta = prm.delta > 0 ? prm.delta : 0.01;
     tol = prm.tol;
     max_iter = prm.max_iter;
     int rc = 0;
@@ -51,9 +51,11 @@ int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStr
         if ((rc = E->alloc_half("cg.Rin", Sp::F32, cap, &Rin)) || (rc = E->alloc_half("cg.Xin", Sp::F32, cap, &Xin)) ||
             (rc = E->alloc_half(tag + ".P", low, cap, &Pl)) || (rc = E->alloc_half(tag + ".T", low, cap, &Tl)) ||
             (rc = E->alloc_half(tag + ".A", low, cap, &Al)) || (rc = E->alloc_half(tag + ".C", low, cap, &Cl)) ||
-            (rc = E->alloc_half("cg.T1", Sp::F64, 1, &T1)) || (rc = E->alloc_half("cg.A1", Sp::F64, 1, &A1)) ||
-            (rc = E->alloc_half("cg.C1", Sp::F64, 1, &C1)))
+            (rc = E->alloc_half("cg.A1", Sp::F64, 1, &A1)) || (rc = E->alloc_half("cg.C1", Sp::F64, 1, &C1)))
             return rc;
+        if ((rc = E->ensure_links(lk, s))) return rc;
+        v2 = hop2_supported(E->ns, low);
+        if (v2 && (rc = E->alloc_half(tag + ".X", low, cap, &Chil))) return rc;
     }
     st = (SysState*)E->get_ws("cg.state", sizeof(SysState) * cap, &rc);
     if (rc) return rc;
@@ -87,11 +89,20 @@ int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStr
     const char* lowname[] = {"f64", "f32", "f16", "bf16"};
     const std::string pre = !mixed ? std::string("f64") :
         std::string("mixed.") + lowname[(int)low] + (lk == Lk::F12 ? ".l12" : ".l18");
+    if (v2) {
+        const std::string p2 = pre + ".v2";
+        pcls[0] = prof_class(p2 + ".K1_chi_minv", n5 * 2 * sp, links);
+        pcls[1] = prof_class(p2 + ".K2_schur_norm_mdinv", n5 * 3 * sp, links);
+        pcls[2] = prof_class(p2 + ".K3_dag_minvdag", n5 * 2 * sp, links);
+        pcls[3] = prof_class(p2 + ".K4_normal_cg", n5 * (3 * sp + 4 * acc), links);
+        pcls[4] = prof_class(p2 + ".P_update_chi", n5 * (acc + 3 * sp), 0.0);
+    } else {
     pcls[0] = prof_class(pre + ".K1_minv", n5 * 2 * sp, links);
     pcls[1] = prof_class(pre + ".K2_schur_norm_mdinv", n5 * 3 * sp, links);
     pcls[2] = prof_class(pre + ".K3_dag_minvdag", n5 * 2 * sp, links);
     pcls[3] = prof_class(pre + ".K4_normal_cg", n5 * (3 * sp + 4 * acc), links);
     pcls[4] = prof_class(pre + ".P_update", n5 * (acc + 2 * sp), 0.0);
+    }
     const double l64 = 8.0 * (double)E->vh() * 144.0;
     pcls_rel[0] = prof_class("f64.reliable.K1_minv", n5 * 2 * 192.0, l64);
     pcls_rel[1] = prof_class("f64.reliable.K2_schur_mdinv", n5 * 3 * 192.0, l64);
@@ -144,7 +155,13 @@ int BatchCG::admit_internal(int slot, cudaStream_t s, double tol_slot, int max_i
     } else {
         ODWF_CK(launch_vec(Sp::F64, Sp::F32, B64.ref(), Rin.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
         ODWF_CK(launch_vec(Sp::F32, Sp::F32, Xin.ref(), Xin.ref(), n5, ns, 5, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
-        ODWF_CK(launch_vec(Sp::F64, low, B64.ref(), Pl.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
+        if (v2) {
+            ODWF_CK(launch_p_update2(low, ns, Rin.ref(), Pl.ref(), Chil.ref(), E->vh(), 0, E->cf32, r_dev, st, 0, 0,
+                                     slot, 1, nullptr, s));
+        } else {
+            ODWF_CK(launch_vec(Sp::F64, low, B64.ref(), Pl.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1,
+                               s));
+        }
     }
     active[slot] = 1;
     n_reliable[slot] = 0;
@@ -195,6 +212,38 @@ int BatchCG::run_iterations(int k, cudaStream_t s) {
                 cudaError_t e_ = launch_vec(Sp::F64, Sp::F64, R64.ref(), P64.ref(), n5, E->ns, 1, 0.0, st, 1, kRunning,
                                             nullptr, nullptr, lo, n, s);
                 set_vec_prof(nullptr);
+                prof_end(pb_, s);
+                ODWF_CK(e_);
+            }
+        } else if (v2) {
+            auto P = params<float>(1);
+            P.gate = 1;
+            P.need_status = kRunning;
+            P.sys_base = lo;
+            const FieldRef ins[4] = {Chil.ref(), Tl.ref(), Al.ref(), Cl.ref()};
+            const FieldRef outs[4] = {Tl.ref(), Al.ref(), Cl.ref(), FieldRef{}};
+            const FieldRef zs[4] = {FieldRef{}, Pl.ref(), FieldRef{}, Al.ref()};
+            for (int k = 0; k < 4; ++k) {
+                P.p_out = (k & 1) ? 0 : 1;
+                P.in = ins[k];
+                P.out = outs[k];
+                P.z = zs[k];
+                if (k == 3) {
+                    P.cg_r = Rin.ref();
+                    P.cg_x = Xin.ref();
+                    P.cg_p = Pl.ref();
+                }
+                auto pb_ = prof_begin(pcls[k], s);
+                P.prof_count = pb_.dev_count;
+                const cudaError_t e_ = launch_hop2(P, k + 1, low, lk, n, s);
+                prof_end(pb_, s);
+                P.prof_count = nullptr;
+                ODWF_CK(e_);
+            }
+            {
+                auto pb_ = prof_begin(pcls[4], s);
+                const cudaError_t e_ = launch_p_update2(low, E->ns, Rin.ref(), Pl.ref(), Chil.ref(), E->vh(), 1, E->cf32,
+                                                        r_dev, st, 1, kRunning, lo, n, pb_.dev_count, s);
                 prof_end(pb_, s);
                 ODWF_CK(e_);
             }
@@ -265,7 +314,7 @@ int BatchCG::any_running() const {
 int BatchCG::fp64_residual(int slot, const HalfField& X, const HalfField& R, cudaStream_t s) {
     FieldRef t, a, c;
     if (mixed) {
-        t = T1.ref_shared();
+        t = R.ref();  // R[slot] is rewritten by the last hop; it holds t = M^-1 H_oe x until then
         a = A1.ref_shared();
         c = C1.ref_shared();
     } else {
@@ -310,8 +359,13 @@ int BatchCG::service(cudaStream_t s) {
         if (mixed) {
             ODWF_CK(launch_vec(Sp::F64, Sp::F32, R64.ref(), Rin.ref(), n5, E->ns, 0, 0.0, st, 1, kRunning, nullptr,
                                nullptr, i, 1, s));
-            ODWF_CK(launch_vec(Sp::F32, low, Rin.ref(), Pl.ref(), n5, E->ns, 1, 0.0, st, 1, kRunning, nullptr, nullptr,
-                               i, 1, s));
+            if (v2) {
+                ODWF_CK(launch_p_update2(low, E->ns, Rin.ref(), Pl.ref(), Chil.ref(), E->vh(), 1, E->cf32, r_dev, st,
+                                         1, kRunning, i, 1, nullptr, s));
+            } else {
+                ODWF_CK(launch_vec(Sp::F32, low, Rin.ref(), Pl.ref(), n5, E->ns, 1, 0.0, st, 1, kRunning, nullptr,
+                                   nullptr, i, 1, s));
+            }
         } else {
             ODWF_CK(launch_vec(Sp::F64, Sp::F64, R64.ref(), P64.ref(), n5, E->ns, 1, 0.0, st, 1, kRunning, nullptr,
                                nullptr, i, 1, s));

@@ -39,7 +39,9 @@ struct BatchCG {
     HalfField P64, T64, A64, C64;  // FP64 CG (mixed = false) operator fields
     HalfField Rin, Xin;            // mixed: FP32 inner residual / solution
     HalfField Pl, Tl, Al, Cl;      // mixed: low-precision operator fields
-    HalfField T1, A1, C1;          // mixed: FP64 temporaries for reliable updates (one system)
+    HalfField Chil;                // mixed (second-generation kernels): chi_p = B p
+    bool v2 = false;               // second-generation mixed kernels (Ns = 8, 16)
+    HalfField A1, C1;              // mixed: FP64 temporaries for reliable updates (one system)
 
     SysState* st = nullptr;        // device [cap]
     SysState* st_host = nullptr;   // pinned mirror

@@ -161,9 +161,9 @@ int Engine::set_gauge(const void* U, cudaStream_t st) {
     }
     const size_t nl = 8 * vh();
     if (!links_d18) ODWF_CK(cudaMalloc(&links_d18, nl * 144));
-    if (!links_f18) ODWF_CK(cudaMalloc(&links_f18, nl * 80));
-    if (!links_f12) ODWF_CK(cudaMalloc(&links_f12, nl * 48));
-    ODWF_CK(launch_pack_links(Ud, links_d18, links_f18, links_f12, g, st));
+    ODWF_CK(launch_pack_links(Ud, links_d18, nullptr, nullptr, g, st));
+    // FP32 copies are derived from the FP64 ones on first use (ensure_links)
+    have_f12 = have_f18 = false;
     if (!is_device_ptr(U)) {
         ODWF_CK(cudaStreamSynchronize(st));
         auto it = ws.find("gauge_stage");  // the staging copy is only needed during packing
@@ -173,6 +173,21 @@ int Engine::set_gauge(const void* U, cudaStream_t st) {
         }
     }
     gauge_set = true;
+    return ODWF_OK;
+}
+
+int Engine::ensure_links(Lk lk, cudaStream_t st) {
+    if (!gauge_set) return fail(ODWF_EINVAL, "gauge field not set");
+    const size_t nl = 8 * vh();
+    if (lk == Lk::F12 && !have_f12) {
+        if (!links_f12) ODWF_CK(cudaMalloc(&links_f12, nl * 48));
+        ODWF_CK(launch_links_from_d18(links_d18, nullptr, links_f12, nl, st));
+        have_f12 = true;
+    } else if (lk == Lk::F18 && !have_f18) {
+        if (!links_f18) ODWF_CK(cudaMalloc(&links_f18, nl * 80));
+        ODWF_CK(launch_links_from_d18(links_d18, links_f18, nullptr, nl, st));
+        have_f18 = true;
+    }
     return ODWF_OK;
 }
 
@@ -378,6 +393,7 @@ int Engine::apply_low_normal(void* out, const void* in, int prec, int recon, cud
         (rc = alloc_half("lo.C", low, 1, &C)))
         return rc;
     const Lk lk = recon == 12 ? Lk::F12 : Lk::F18;
+    if ((rc = ensure_links(lk, st))) return rc;
     ODWF_CK(launch_pack(low, din, X.ref_sys(0), g, 0, ns, 1, st));
     auto P = hop_params<float>(1, rd);
     P.links = recon == 12 ? links_f12 : links_f18;

@@ -61,6 +61,7 @@ struct Engine {
     void* links_f18 = nullptr;
     void* links_f12 = nullptr;
     bool gauge_set = false;
+    bool have_f12 = false, have_f18 = false;  // FP32 link copies derived from the FP64 ones
 
     // named workspaces (grow-only)
     std::map<std::string, DevBuf> ws;
@@ -70,6 +71,7 @@ struct Engine {
     ~Engine();
     int init(const odwf_lattice* l, int Ns, double m0_, double mq_, const double* w);
     int set_gauge(const void* U, cudaStream_t st);
+    int ensure_links(Lk lk, cudaStream_t st);  // FP32 links in format lk, converted on first use
 
     size_t vh() const { return (size_t)g.Vh; }
     size_t sites5() const { return (size_t)g.Vh * ns; }

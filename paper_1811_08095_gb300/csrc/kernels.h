@@ -40,6 +40,16 @@ cudaError_t launch_hop_f64(const HopParams<double>& P, Epi e, int nsys, cudaStre
 // Mixed path (low-precision operator fields, FP32 accumulators r/x, float links, FP32 arithmetic)
 cudaError_t launch_hop_mixed(const HopParams<float>& P, Epi e, Sp low, Lk lk, int nsys, cudaStream_t st);
 
+// Second-generation mixed CG kernels (Ns = 8 or 16): kind 1..4 = K1..K4 of the iteration
+// (see kernels_mixed2.cu); the non-dagger hops read chi = B psi fields.
+bool hop2_supported(int ns, Sp low);
+cudaError_t launch_hop2(const HopParams<float>& P, int kind, Sp low, Lk lk, int nsys, cudaStream_t st);
+// p = r (mode 0) or p = r + beta p (mode 1), and chi = B p
+cudaError_t launch_p_update2(Sp low, int ns, const FieldRef& r, const FieldRef& p, const FieldRef& chi,
+                             size_t n_sites, int mode, const Coef5<float>& cf, const double* r_sys, SysState* st,
+                             int gate, int need, int sys_base, int nsys, unsigned long long* prof,
+                             cudaStream_t stream);
+
 // Site-local M, M^dag, M^-1, M^-dag (op 0..3)
 cudaError_t launch_m5_f64(const FieldRef& in, const FieldRef& out, size_t n_sites, int ns, const double* r_sys,
                           int sys_base, int nsys, int op, const Coef5<double>& cf, cudaStream_t st);
@@ -65,6 +75,9 @@ cudaError_t launch_state(SysState* st, int nsys, int mode, double tol2, cudaStre
 
 // Gauge packing from external complex128 U[mu][t][z][y][x][3][3] (device)
 cudaError_t launch_pack_links(const double2* U, void* d18, void* f18, void* f12, const Geom& g, cudaStream_t st);
+
+// FP32 links (18 reals padded to 20, or the first two rows) from the packed FP64 links
+cudaError_t launch_links_from_d18(const void* d18, void* f18, void* f12, size_t n_links, cudaStream_t st);
 
 int lg2(int v);
 

@@ -202,6 +202,26 @@ __global__ void pack_links_kernel(const double2* __restrict__ U, double* d18, fl
     if (f18) { f18[o * 20 + 18] = 0.f; f18[o * 20 + 19] = 0.f; }
 }
 
+__global__ void links_from_d18_kernel(const double* __restrict__ d18, float* f18, float* f12, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* src = d18 + i * 18;
+    if (f18) {
+        for (int k = 0; k < 18; ++k) f18[i * 20 + k] = (float)src[k];
+        f18[i * 20 + 18] = 0.f;
+        f18[i * 20 + 19] = 0.f;
+    }
+    if (f12)
+        for (int k = 0; k < 12; ++k) f12[i * 12 + k] = (float)src[k];
+}
+
+cudaError_t launch_links_from_d18(const void* d18, void* f18, void* f12, size_t n_links, cudaStream_t st) {
+    note_launch();
+    links_from_d18_kernel<<<blocks_for(n_links, 256), 256, 0, st>>>((const double*)d18, (float*)f18, (float*)f12,
+                                                                     n_links);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack_links(const double2* U, void* d18, void* f18, void* f12, const Geom& g, cudaStream_t st) {
     const size_t n = 8 * (size_t)g.Vh;
     note_launch(); pack_links_kernel<<<blocks_for(n, 256), 256, 0, st>>>(U, (double*)d18, (float*)f18, (float*)f12, g);

@@ -1,0 +1,508 @@
+// Mixed-precision CG kernels, second generation (Ns = 8, 16; FP16 / BF16 / FP32 storage).
+//
+// The non-dagger hops read the chirally shifted field chi = B psi, written by the kernel
+// that produces psi, so B is applied once per site on the producing side instead of once
+// per (site, direction) on the consuming side:
+//   P   p = r + beta p;  chi_p = B p                                   (stores p, chi_p)
+//   K1  chi_t = B M^-1 (-1/2 W chi_p)                                  (t = M^-1 H_oe p)
+//   K2  s = p - M^-1 (-1/2 W chi_t);  |s|^2 -> alpha;  a = M^-dag s    (s = S p)
+//   K3  c = M^-dag (-1/2 B^dag W^dag a)
+//   K4  A p = M^dag a + 1/2 B^dag W^dag c;  r -= alpha A p;  x += alpha p;  |r|^2 -> beta
+// The eight links of an output site are loaded (and, for 12-real storage, completed to
+// 18 reals) once per site: lane d < 8 of the site's lane group handles direction d and
+// leaves it in shared memory, which the group's Ns lanes then read (the group lies in one
+// warp, so a warp barrier suffices).  The per-site FP16/BF16 scale and the time-boundary
+// sign of each neighbour are folded into the FMAs that accumulate its contribution.  Ns
+// is a template parameter, so the fifth-dimension scans unroll.
+#include "kernels.cuh"
+#include "kernels.h"
+
+namespace odwf {
+
+namespace {
+
+constexpr int kBS2 = 256;
+
+// raw stored values (not scaled) and the scale of one 5D site
+template <class SP>
+struct RawIO;
+
+template <>
+struct RawIO<SpF32> {
+    static __device__ __forceinline__ float load(const void* base, const float*, size_t h, int s, int ns, float v[24]) {
+        const float4* p = reinterpret_cast<const float4*>(base);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 q = __ldg(p + chunk_off(h, k, 6, ns, s));
+            v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
+        }
+        return 1.f;
+    }
+};
+
+template <class H2>
+struct RawHalfIO {
+    static __device__ __forceinline__ float load(const void* base, const float* norm, size_t h, int s, int ns,
+                                                 float v[24]) {
+        const uint4* p = reinterpret_cast<const uint4*>(base);
+        const float sc = __ldg(norm + h * ns + s);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint4 q = __ldg(p + chunk_off(h, k, 3, ns, s));
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                H2 hv;
+                *reinterpret_cast<uint32_t*>(&hv) = w[j];
+                const float2 f = Half2Cvt<H2>::to_f2(hv);
+                v[8 * k + 2 * j] = f.x;
+                v[8 * k + 2 * j + 1] = f.y;
+            }
+        }
+        return sc;
+    }
+};
+template <>
+struct RawIO<SpF16> : RawHalfIO<__half2> {};
+template <>
+struct RawIO<SpBF16> : RawHalfIO<__nv_bfloat162> {};
+
+enum { K1 = 1, K2 = 2, K3 = 3, K4 = 4 };
+
+// acc += m_up * w (upper spins) and acc_dn += m_dn * G^dag w (lower spins)
+__device__ __forceinline__ void accumulate_scaled(int mu, float m_up, float m_dn, const float w[12], float acc[24]) {
+    const float* w0 = w;
+    const float* w1 = w + 6;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[2 * c] = fmaf(m_up, w0[2 * c], acc[2 * c]);
+        acc[2 * c + 1] = fmaf(m_up, w0[2 * c + 1], acc[2 * c + 1]);
+        acc[6 + 2 * c] = fmaf(m_up, w1[2 * c], acc[6 + 2 * c]);
+        acc[6 + 2 * c + 1] = fmaf(m_up, w1[2 * c + 1], acc[6 + 2 * c + 1]);
+        float l0r, l0i, l1r, l1i;
+        switch (mu) {
+            case 0: l0r = -w1[2 * c + 1]; l0i = w1[2 * c]; l1r = -w0[2 * c + 1]; l1i = w0[2 * c]; break;
+            case 1: l0r = w1[2 * c]; l0i = w1[2 * c + 1]; l1r = -w0[2 * c]; l1i = -w0[2 * c + 1]; break;
+            case 2: l0r = -w0[2 * c + 1]; l0i = w0[2 * c]; l1r = w1[2 * c + 1]; l1i = -w1[2 * c]; break;
+            default: l0r = w0[2 * c]; l0i = w0[2 * c + 1]; l1r = w1[2 * c]; l1i = w1[2 * c + 1]; break;
+        }
+        acc[12 + 2 * c] = fmaf(m_dn, l0r, acc[12 + 2 * c]);
+        acc[12 + 2 * c + 1] = fmaf(m_dn, l0i, acc[12 + 2 * c + 1]);
+        acc[18 + 2 * c] = fmaf(m_dn, l1r, acc[18 + 2 * c]);
+        acc[18 + 2 * c + 1] = fmaf(m_dn, l1i, acc[18 + 2 * c + 1]);
+    }
+}
+
+// Unscaled projection h = v^up + sg G v^dn (the scale is applied at accumulation)
+__device__ __forceinline__ void project_raw(int mu, float sg, const float v[24], float h[12]) { project(mu, sg, v, h); }
+
+
+// ---------------------------------------------------------------- packed FP32 pairs
+// A "spin pair" holds one colour and one real/imaginary part of the two spins of a
+// chirality half: R[c] = (spin_a.re, spin_b.re), I[c] = (spin_a.im, spin_b.im).  Pair
+// arithmetic uses the FP32x2 FMA of sm_100+ (one instruction for two lanes of work).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Load one 5D site as spin pairs: up half (spins 0, 1) and down half (spins 2, 3; in the
+// order (3, 2) when SWAP_DN).  Returns the site's scale.
+template <class SP, bool SWAP_DN>
+struct PackedLoad;
+
+template <class H2, bool SWAP_DN>
+struct PackedHalfLoad {
+    static __device__ __forceinline__ float load(const void* base, const float* norm, size_t h, int s, int ns,
+                                                 float2 Ur[3], float2 Ui[3], float2 Dr[3], float2 Di[3]) {
+        const uint4* p = reinterpret_cast<const uint4*>(base);
+        const float sc = __ldg(norm + h * ns + s);
+        float2 f[12];  // word w = (spin w/3, colour w%3): (re, im)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint4 q = __ldg(p + chunk_off(h, k, 3, ns, s));
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                H2 hv;
+                *reinterpret_cast<uint32_t*>(&hv) = w[j];
+                f[4 * k + j] = Half2Cvt<H2>::to_f2(hv);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Ur[c] = make_float2(f[c].x, f[3 + c].x);
+            Ui[c] = make_float2(f[c].y, f[3 + c].y);
+            if (SWAP_DN) {
+                Dr[c] = make_float2(f[9 + c].x, f[6 + c].x);
+                Di[c] = make_float2(f[9 + c].y, f[6 + c].y);
+            } else {
+                Dr[c] = make_float2(f[6 + c].x, f[9 + c].x);
+                Di[c] = make_float2(f[6 + c].y, f[9 + c].y);
+            }
+        }
+        return sc;
+    }
+};
+template <bool SW>
+struct PackedLoad<SpF16, SW> : PackedHalfLoad<__half2, SW> {};
+template <bool SW>
+struct PackedLoad<SpBF16, SW> : PackedHalfLoad<__nv_bfloat162, SW> {};
+template <bool SWAP_DN>
+struct PackedLoad<SpF32, SWAP_DN> {
+    static __device__ __forceinline__ float load(const void* base, const float*, size_t h, int s, int ns,
+                                                 float2 Ur[3], float2 Ui[3], float2 Dr[3], float2 Di[3]) {
+        float v[24];
+        RawIO<SpF32>::load(base, nullptr, h, s, ns, v);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Ur[c] = make_float2(v[2 * c], v[6 + 2 * c]);
+            Ui[c] = make_float2(v[2 * c + 1], v[6 + 2 * c + 1]);
+            const int a = SWAP_DN ? 18 : 12, b = SWAP_DN ? 12 : 18;
+            Dr[c] = make_float2(v[a + 2 * c], v[b + 2 * c]);
+            Di[c] = make_float2(v[a + 2 * c + 1], v[b + 2 * c + 1]);
+        }
+        return 1.f;
+    }
+};
+
+// One hop direction in spin pairs.  H = v^up + sg G v^dn (G of gamma_mu in the chiral basis,
+// gamma_mu = [[0, G], [G^dag, 0]]); W = U H (or U^dag H); then
+//   AU += sc W,  lower spins += sg sc G^dag W,
+// accumulated in AD (order (2, 3)) for mu = 2, 3 and in ADS (order (3, 2)) for mu = 0, 1, so
+// that no pair ever needs its halves exchanged.  The link comes from shared memory as nine
+// float4 (ur, ur, ui, ui), element (a, b) at index 3a + b.
+template <class SP, int MU, bool DAGU>
+__device__ __forceinline__ void hop_dir_packed(const void* in, const float* in_n, size_t hn, int s, int ns,
+                                               bool valid, float sc_sign, float sg, const float4* lnk,
+                                               float2 AUr[3], float2 AUi[3], float2 ADr[3], float2 ADi[3],
+                                               float2 ADSr[3], float2 ADSi[3]) {
+    constexpr bool SW = (MU == 0 || MU == 1);
+    float2 Ur[3], Ui[3], Dr[3], Di[3];
+    float sc = 0.f;
+    if (valid) {
+        sc = PackedLoad<SP, SW>::load(in, in_n, hn, s, ns, Ur, Ui, Dr, Di);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Ur[c] = Ui[c] = Dr[c] = Di[c] = make_float2(0.f, 0.f);
+    }
+    sc *= sc_sign;
+    // projection
+    float2 Hr[3], Hi[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (MU == 0) {          // G = -i s1:  G d = -i (d1, d0)
+            Hr[c] = fma2(Di[c], make_float2(sg, sg), Ur[c]);
+            Hi[c] = fma2(Dr[c], make_float2(-sg, -sg), Ui[c]);
+        } else if (MU == 1) {   // G = -i s2:  G d = (-d1, d0)
+            Hr[c] = fma2(Dr[c], make_float2(-sg, sg), Ur[c]);
+            Hi[c] = fma2(Di[c], make_float2(-sg, sg), Ui[c]);
+        } else if (MU == 2) {   // G = -i s3:  G d = (-i d0, i d1)
+            Hr[c] = fma2(Di[c], make_float2(sg, -sg), Ur[c]);
+            Hi[c] = fma2(Dr[c], make_float2(-sg, sg), Ui[c]);
+        } else {                // G = 1
+            Hr[c] = fma2(Dr[c], make_float2(sg, sg), Ur[c]);
+            Hi[c] = fma2(Di[c], make_float2(sg, sg), Ui[c]);
+        }
+    }
+    // SU(3) product
+    float2 Nh[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Nh[c] = DAGU ? make_float2(-Hr[c].x, -Hr[c].y) : make_float2(-Hi[c].x, -Hi[c].y);
+    float2 Wr[3], Wi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        Wr[a] = make_float2(0.f, 0.f);
+        Wi[a] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float4 q = lnk[DAGU ? 3 * b + a : 3 * a + b];
+            const float2 ur = make_float2(q.x, q.y), ui = make_float2(q.z, q.w);
+            if (!DAGU) {
+                Wr[a] = fma2(ur, Hr[b], fma2(ui, Nh[b], Wr[a]));
+                Wi[a] = fma2(ur, Hi[b], fma2(ui, Hr[b], Wi[a]));
+            } else {
+                Wr[a] = fma2(ur, Hr[b], fma2(ui, Hi[b], Wr[a]));
+                Wi[a] = fma2(ur, Hi[b], fma2(ui, Nh[b], Wi[a]));
+            }
+        }
+    }
+    // accumulation
+    const float m = sc, md = sg * sc;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        AUr[a] = fma2(make_float2(m, m), Wr[a], AUr[a]);
+        AUi[a] = fma2(make_float2(m, m), Wi[a], AUi[a]);
+        if (MU == 0) {          // G^dag = i s1: lower (3, 2) order = i W
+            ADSr[a] = fma2(make_float2(-md, -md), Wi[a], ADSr[a]);
+            ADSi[a] = fma2(make_float2(md, md), Wr[a], ADSi[a]);
+        } else if (MU == 1) {   // G^dag = [[0, 1], [-1, 0]]: lower (3, 2) order = W (-1, 1)
+            ADSr[a] = fma2(make_float2(-md, md), Wr[a], ADSr[a]);
+            ADSi[a] = fma2(make_float2(-md, md), Wi[a], ADSi[a]);
+        } else if (MU == 2) {   // G^dag = i s3: lower = (i w0, -i w1)
+            ADr[a] = fma2(make_float2(-md, md), Wi[a], ADr[a]);
+            ADi[a] = fma2(make_float2(md, -md), Wr[a], ADi[a]);
+        } else {                // G^dag = 1
+            ADr[a] = fma2(make_float2(md, md), Wr[a], ADr[a]);
+            ADi[a] = fma2(make_float2(md, md), Wi[a], ADi[a]);
+        }
+    }
+}
+
+constexpr int kLinkStride = 36;                  // floats per staged link: 9 x (ur, ur, ui, ui)
+constexpr int kSiteLinks = 8 * kLinkStride + 4;  // floats per site (padding spreads banks)
+
+template <class SP, class LK, int NS, int KIND>
+__global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P) {
+    constexpr bool DAG = (KIND == K3 || KIND == K4);
+    const int sys = blockIdx.y + P.sys_base;
+    if (P.gate && P.st[sys].status != P.need_status) return;
+    if (P.prof_count && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(P.prof_count, 1ull);
+
+    const size_t gi = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = (int)(gi & (NS - 1));
+    const size_t hh = gi / NS;
+    const bool valid = hh < (size_t)P.g.Vh;
+    const int h = valid ? (int)hh : 0;
+    const float r = (float)P.r_sys[sys];
+    const int p_out = P.p_out, p_in = 1 - p_out;
+
+    // the eight neighbours of this site: half index and time-boundary sign
+    int c[4];
+    site_coords(P.g, p_out, h, c);
+    int nb[8];
+    unsigned flip = 0;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        const int Lm = P.g.L[mu];
+        int cf[4] = {c[0], c[1], c[2], c[3]}, cb[4] = {c[0], c[1], c[2], c[3]};
+        cf[mu] = c[mu] + 1 == Lm ? 0 : c[mu] + 1;
+        cb[mu] = c[mu] == 0 ? Lm - 1 : c[mu] - 1;
+        nb[2 * mu] = half_index(P.g, cf);
+        nb[2 * mu + 1] = half_index(P.g, cb);
+    }
+    if (P.g.tbc) {
+        if (c[3] == P.g.L[3] - 1) flip |= 1u << 6;
+        if (c[3] == 0) flip |= 1u << 7;
+    }
+
+    // stage the site's eight links in shared memory: lane d < 8 of the group loads direction d
+    __shared__ __align__(16) float s_links[(kBS2 / NS) * kSiteLinks];
+    float* my_links = s_links + (threadIdx.x / NS) * kSiteLinks;
+    if (s < 8) {
+        const int mu = s >> 1, dir = s & 1;
+        const size_t lidx = dir == 0 ? ((size_t)(p_out * 4 + mu) * P.g.Vh + h)
+                                     : ((size_t)(p_in * 4 + mu) * P.g.Vh + nb[s]);
+        float u[18];
+        LinkIO<LK, float>::load(P.links, lidx, u);
+        float4* dst = reinterpret_cast<float4*>(my_links + s * kLinkStride);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) dst[k] = make_float4(u[2 * k], u[2 * k], u[2 * k + 1], u[2 * k + 1]);
+    }
+    __syncwarp();
+
+    const void* in = P.in.d(sys);
+    const float* in_n = P.in.n(sys);
+    (void)&project_raw;
+    float2 AUr[3], AUi[3], ADr[3], ADi[3], ADSr[3], ADSi[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) AUr[c] = AUi[c] = ADr[c] = ADi[c] = ADSr[c] = ADSi[c] = make_float2(0.f, 0.f);
+    const float4* L4 = reinterpret_cast<const float4*>(my_links);
+    // forward hops use (1 - gamma) for D and (1 + gamma) for D^dag; backward the opposite
+    constexpr float SF = DAG ? 1.f : -1.f;
+#define ODWF_HOP_DIR(MU_, DIR_)                                                                                   \
+    hop_dir_packed<SP, MU_, DIR_ == 1>(in, in_n, (size_t)nb[2 * MU_ + DIR_], s, NS, valid,                        \
+                                       (flip & (1u << (2 * MU_ + DIR_))) ? -1.f : 1.f, DIR_ == 0 ? SF : -SF,     \
+                                       L4 + (2 * MU_ + DIR_) * 9, AUr, AUi, ADr, ADi, ADSr, ADSi)
+    ODWF_HOP_DIR(0, 0); ODWF_HOP_DIR(0, 1);
+    ODWF_HOP_DIR(1, 0); ODWF_HOP_DIR(1, 1);
+    ODWF_HOP_DIR(2, 0); ODWF_HOP_DIR(2, 1);
+    ODWF_HOP_DIR(3, 0); ODWF_HOP_DIR(3, 1);
+#undef ODWF_HOP_DIR
+    float acc[24];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[2 * c] = AUr[c].x;
+        acc[2 * c + 1] = AUi[c].x;
+        acc[6 + 2 * c] = AUr[c].y;
+        acc[6 + 2 * c + 1] = AUi[c].y;
+        acc[12 + 2 * c] = ADr[c].x + ADSr[c].y;
+        acc[12 + 2 * c + 1] = ADi[c].x + ADSi[c].y;
+        acc[18 + 2 * c] = ADr[c].y + ADSr[c].x;
+        acc[18 + 2 * c + 1] = ADi[c].y + ADSi[c].x;
+    }
+
+    const Coef5<float>& cf = P.cf;
+    double nrm = 0.0;
+    if (KIND == K1) {
+        // chi_t = B M^-1 (-1/2 y)
+#pragma unroll
+        for (int k = 0; k < 24; ++k) acc[k] *= -0.5f;
+        minv_apply(acc, cf, r, s, NS, false);
+        bidiag_apply(acc, cf.rho[s], cf.sigma[s], r, s, NS, false);
+        if (valid) SpinorIO<SP, float>::store(P.out.d(sys), P.out.n(sys), (size_t)h, s, NS, acc);
+    } else if (KIND == K2) {
+        // s = p - M^-1 (-1/2 y) = p + M^-1 (y/2);  |s|^2;  a = M^-dag s
+#pragma unroll
+        for (int k = 0; k < 24; ++k) acc[k] *= 0.5f;
+        minv_apply(acc, cf, r, s, NS, false);
+        float z[24];
+        if (valid) {
+            SpinorIO<SP, float>::load(P.z.d(sys), P.z.n(sys), (size_t)h, s, NS, z);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 24; ++k) z[k] = 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 24; ++k) {
+            acc[k] += z[k];
+            nrm += (double)acc[k] * (double)acc[k];
+        }
+        minv_apply(acc, cf, r, s, NS, true);
+        if (valid) SpinorIO<SP, float>::store(P.out.d(sys), P.out.n(sys), (size_t)h, s, NS, acc);
+    } else if (KIND == K3) {
+        // c = M^-dag (-1/2 B^dag y)
+        bidiag_apply(acc, cf.rho[s], cf.sigma[s], r, s, NS, true);
+#pragma unroll
+        for (int k = 0; k < 24; ++k) acc[k] *= -0.5f;
+        minv_apply(acc, cf, r, s, NS, true);
+        if (valid) SpinorIO<SP, float>::store(P.out.d(sys), P.out.n(sys), (size_t)h, s, NS, acc);
+    } else {
+        // A p = M^dag a + 1/2 B^dag y;  r -= alpha A p;  x += alpha p
+        bidiag_apply(acc, cf.rho[s], cf.sigma[s], r, s, NS, true);
+        float z[24];
+        if (valid) {
+            SpinorIO<SP, float>::load(P.z.d(sys), P.z.n(sys), (size_t)h, s, NS, z);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 24; ++k) z[k] = 0.f;
+        }
+        bidiag_apply(z, cf.d[s], cf.e[s], r, s, NS, true);
+        const float alpha = (float)P.st[sys].alpha;
+        if (valid) {
+            float rv[24], xv[24], pv[24];
+            SpinorIO<SpF32, float>::load(P.cg_r.d(sys), nullptr, (size_t)h, s, NS, rv);
+            SpinorIO<SpF32, float>::load(P.cg_x.d(sys), nullptr, (size_t)h, s, NS, xv);
+            SpinorIO<SP, float>::load(P.cg_p.d(sys), P.cg_p.n(sys), (size_t)h, s, NS, pv);
+#pragma unroll
+            for (int k = 0; k < 24; ++k) {
+                const float ap = fmaf(0.5f, acc[k], z[k]);
+                rv[k] = fmaf(-alpha, ap, rv[k]);
+                xv[k] = fmaf(alpha, pv[k], xv[k]);
+                nrm += (double)rv[k] * (double)rv[k];
+            }
+            SpinorIO<SpF32, float>::store(P.cg_r.d(sys), nullptr, (size_t)h, s, NS, rv);
+            SpinorIO<SpF32, float>::store(P.cg_x.d(sys), nullptr, (size_t)h, s, NS, xv);
+        }
+    }
+    if (KIND == K2) reduce_and_finalize(nrm, P.partials, P.counters, P.st, sys, FIN_ALPHA);
+    if (KIND == K4) reduce_and_finalize(nrm, P.partials, P.counters, P.st, sys, FIN_BETA);
+}
+
+// p = r + beta p (mode 1) or p = r (mode 0);  chi = B p.  One thread per (site, s), lane groups of NS.
+template <class SP, int NS>
+__global__ void __launch_bounds__(kBS2) p_update2_kernel(FieldRef rr, FieldRef pp, FieldRef chi, size_t n_sites,
+                                                          int mode, Coef5<float> cf, const double* r_sys,
+                                                          SysState* st, int gate, int need, int sys_base,
+                                                          unsigned long long* prof_count) {
+    const int sys = blockIdx.y + sys_base;
+    if (gate && st[sys].status != need) return;
+    if (prof_count && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(prof_count, 1ull);
+    const size_t gi = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = (int)(gi & (NS - 1));
+    const size_t h = gi / NS;
+    const bool valid = h < n_sites;
+    float v[24];
+    if (valid) {
+        SpinorIO<SpF32, float>::load(rr.d(sys), nullptr, h, s, NS, v);
+        if (mode == 1) {
+            const float beta = (float)st[sys].beta;
+            float pv[24];
+            SpinorIO<SP, float>::load(pp.d(sys), pp.n(sys), h, s, NS, pv);
+#pragma unroll
+            for (int k = 0; k < 24; ++k) v[k] = fmaf(beta, pv[k], v[k]);
+        }
+        SpinorIO<SP, float>::store(pp.d(sys), pp.n(sys), h, s, NS, v);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 24; ++k) v[k] = 0.f;
+    }
+    // chi = B p, from the stored (rounded) p so that chi matches the p the hops see
+    if (valid) SpinorIO<SP, float>::load(pp.d(sys), pp.n(sys), h, s, NS, v);
+    bidiag_apply(v, cf.rho[s], cf.sigma[s], (float)r_sys[sys], s, NS, false);
+    if (valid) SpinorIO<SP, float>::store(chi.d(sys), chi.n(sys), h, s, NS, v);
+}
+
+template <class SP, class LK, int NS>
+cudaError_t hop2_k(const HopParams<float>& P, int kind, int nsys, cudaStream_t st) {
+    const size_t n = (size_t)P.g.Vh * NS;
+    dim3 grid(blocks_for(n, kBS2), nsys);
+    note_launch();
+    switch (kind) {
+        case K1: hop2_kernel<SP, LK, NS, K1><<<grid, kBS2, 0, st>>>(P); break;
+        case K2: hop2_kernel<SP, LK, NS, K2><<<grid, kBS2, 0, st>>>(P); break;
+        case K3: hop2_kernel<SP, LK, NS, K3><<<grid, kBS2, 0, st>>>(P); break;
+        default: hop2_kernel<SP, LK, NS, K4><<<grid, kBS2, 0, st>>>(P); break;
+    }
+    return cudaGetLastError();
+}
+
+template <class SP, class LK>
+cudaError_t hop2_ns(const HopParams<float>& P, int kind, int nsys, cudaStream_t st) {
+    switch (P.ns) {
+        case 8: return hop2_k<SP, LK, 8>(P, kind, nsys, st);
+        case 16: return hop2_k<SP, LK, 16>(P, kind, nsys, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class SP>
+cudaError_t hop2_lk(const HopParams<float>& P, int kind, Lk lk, int nsys, cudaStream_t st) {
+    return lk == Lk::F12 ? hop2_ns<SP, LinkF12>(P, kind, nsys, st) : hop2_ns<SP, LinkF18>(P, kind, nsys, st);
+}
+
+template <class SP, int NS>
+cudaError_t pupd_k(const FieldRef& r, const FieldRef& p, const FieldRef& chi, size_t n_sites, int mode,
+                   const Coef5<float>& cf, const double* r_sys, SysState* st, int gate, int need, int sys_base,
+                   int nsys, unsigned long long* prof, cudaStream_t stream) {
+    dim3 grid(blocks_for(n_sites * NS, kBS2), nsys);
+    note_launch();
+    p_update2_kernel<SP, NS><<<grid, kBS2, 0, stream>>>(r, p, chi, n_sites, mode, cf, r_sys, st, gate, need,
+                                                         sys_base, prof);
+    return cudaGetLastError();
+}
+
+template <class SP>
+cudaError_t pupd_ns(int ns, const FieldRef& r, const FieldRef& p, const FieldRef& chi, size_t n_sites, int mode,
+                    const Coef5<float>& cf, const double* r_sys, SysState* st, int gate, int need, int sys_base,
+                    int nsys, unsigned long long* prof, cudaStream_t stream) {
+    switch (ns) {
+        case 8: return pupd_k<SP, 8>(r, p, chi, n_sites, mode, cf, r_sys, st, gate, need, sys_base, nsys, prof, stream);
+        case 16: return pupd_k<SP, 16>(r, p, chi, n_sites, mode, cf, r_sys, st, gate, need, sys_base, nsys, prof, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+bool hop2_supported(int ns, Sp low) { return (ns == 8 || ns == 16) && (low == Sp::F16 || low == Sp::BF16 || low == Sp::F32); }
+
+cudaError_t launch_hop2(const HopParams<float>& P, int kind, Sp low, Lk lk, int nsys, cudaStream_t st) {
+    switch (low) {
+        case Sp::F16: return hop2_lk<SpF16>(P, kind, lk, nsys, st);
+        case Sp::BF16: return hop2_lk<SpBF16>(P, kind, lk, nsys, st);
+        case Sp::F32: return hop2_lk<SpF32>(P, kind, lk, nsys, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_p_update2(Sp low, int ns, const FieldRef& r, const FieldRef& p, const FieldRef& chi,
+                             size_t n_sites, int mode, const Coef5<float>& cf, const double* r_sys, SysState* st,
+                             int gate, int need, int sys_base, int nsys, unsigned long long* prof,
+                             cudaStream_t stream) {
+    switch (low) {
+        case Sp::F16: return pupd_ns<SpF16>(ns, r, p, chi, n_sites, mode, cf, r_sys, st, gate, need, sys_base, nsys, prof, stream);
+        case Sp::BF16: return pupd_ns<SpBF16>(ns, r, p, chi, n_sites, mode, cf, r_sys, st, gate, need, sys_base, nsys, prof, stream);
+        case Sp::F32: return pupd_ns<SpF32>(ns, r, p, chi, n_sites, mode, cf, r_sys, st, gate, need, sys_base, nsys, prof, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace odwf

@@ -164,7 +164,7 @@ bool try_admit(serve_handle* S, const std::shared_ptr<Request>& R, std::unique_l
         prm.tol = q.tol;
         prm.max_iter = q.max_iter;
         prm.prec = q.prec;
-        prm.delta = 0.1;
+        prm.delta = 0.01;
         g->cg = std::make_unique<BatchCG>();
         if (!rc) rc = g->cg->init(g->eng.get(), cap, prm, g->stream);
         lk.lock();

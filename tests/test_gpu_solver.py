@@ -74,6 +74,23 @@ def test_cg_ragged_ns16_host_pointers(torch, prec):
     h.close()
 
 
+@pytest.mark.parametrize("ns,prec", [(4, "f16"), (2, "bf16"), (32, "f32")])
+def test_cg_generic_kernel_ns(torch, ns, prec):
+    """Ns outside {8, 16} runs the generic mixed kernels; same bar."""
+    dims, mq = (4, 2, 4, 4), 0.03
+    U, w = make_case(dims, ns, mq, eps=0.3, seed=5)
+    b = syn.gaussian_spinor_even(ns, dims, 102)
+    h = odwf.Handle(dims, ns, M0, mq, w)
+    h.set_gauge(U)
+    x = np.zeros_like(b)
+    st = h.cg_solve(x, b, tol=1e-10, max_iter=20000, prec=prec)
+    assert st["status"] == 0
+    assert _true_resid(U, x, b, mq, w) <= 1e-10
+    x_ref, _, _ = oracle.cg(U, b, M0, mq, w, tol=1e-13)
+    assert rel_norm(x, x_ref) <= 1e-8
+    h.close()
+
+
 def test_batched_multi_mass_multi_rhs(torch):
     dims, ns = (4, 4, 4, 8), 8
     U, w = make_case(dims, ns, 0.01, eps=0.25, seed=3)
