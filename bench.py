@@ -342,6 +342,234 @@ def run_ours(args, world, rank, local):
         dist.destroy_process_group()
 
 
+SERVE_LATTICES = [(8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 48), (32, 32, 32, 32)]
+
+
+def run_serve(args, world, rank, local):
+    """Serving stream: Poisson arrivals of D^dag D solve requests over four resident fields
+    (8^4, 16^4, 24^3x48, 32^4; links exp(0.25 i H), seeds 11-14), Ns in {8, 16}, m_q uniform
+    in [0.002, 0.5], 1-12 right-hand sides each, mixed precision to 1e-10.  Reports p50 / p99
+    latency of the completed requests, throughput, and how many were still pending at the end.
+    The load generator reuses pools of right-hand sides and output buffers (results of this
+    timing run are not kept; served results are checked by tests/test_gpu_serving.py)."""
+    import numpy as np
+    import torch
+
+    import odwf_synth as syn
+    import paper_1811_08095_gb300 as odwf
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rng = np.random.default_rng(21)
+    srv = odwf.Server(0)
+    vols = []
+    for k, dims in enumerate(SERVE_LATTICES):
+        U = syn.gauge_field_torch(dims, EPS, 11 + k, device=dev)
+        srv.register_gauge(k, dims, U)
+        vols.append(dims[0] * dims[1] * dims[2] * dims[3])
+        del U
+    omegas = {ns: odwf.odwf_zolotarev_omega(ns, LRANGE[0], LRANGE[1])[0] for ns in (8, 16)}
+    pool = {}
+    g = torch.Generator(device=dev)
+    g.manual_seed(1234)
+    for k in range(len(SERVE_LATTICES)):
+        for ns in (8, 16):
+            shape = (ns, vols[k] // 2, 4, 3)
+            bs = [torch.randn(shape, dtype=torch.complex128, device=dev, generator=g) for _ in range(12)]
+            xs = [torch.zeros(shape, dtype=torch.complex128, device=dev) for _ in range(12)]
+            pool[(k, ns)] = (bs, xs)
+    torch.cuda.synchronize()
+    rate, duration, drain = args.rate, args.duration, args.drain
+    t0 = time.perf_counter()
+    next_t = t0 + rng.exponential(1.0 / rate)
+    pending, done, submitted, solves_done = {}, [], 0, 0
+    while True:
+        now = time.perf_counter()
+        if now - t0 < duration and now >= next_t:
+            k = int(rng.integers(0, len(SERVE_LATTICES)))
+            ns = int(rng.choice([8, 16]))
+            mq = float(rng.uniform(0.002, 0.5))
+            nrhs = int(rng.integers(1, 13))
+            bs, xs = pool[(k, ns)]
+            t = srv.submit(k, ns, M0, mq, omegas[ns], bs[:nrhs], xs[:nrhs], tol=TOL, prec=args.prec)
+            pending[t] = (nrhs, k, ns)
+            submitted += 1
+            next_t += rng.exponential(1.0 / rate)
+            continue
+        for t in list(pending):
+            rc, res = srv.poll(t, 0)
+            if rc != odwf._lib.ODWF_PENDING:
+                nrhs, k, ns = pending.pop(t)
+                done.append((res["latency_ms"], res["queue_ms"], rc, nrhs, k, ns, res["true_resid"]))
+                solves_done += nrhs
+        if now - t0 >= duration and (not pending or now - t0 >= duration + drain):
+            break
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    lat = np.array([d[0] for d in done]) if done else np.array([float("nan")])
+    bad = [d for d in done if d[2] != 0]
+    line = {"metric": "served ODWF D\u2020D solve latency (p50/p99) and throughput", "workload": "serve_poisson",
+            "rate_req_s": rate, "duration_s": duration, "submitted": submitted, "completed": len(done),
+            "pending_at_end": len(pending), "failed": len(bad), "wall_s": round(wall, 2),
+            "p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2),
+            "throughput_req_s": round(len(done) / wall, 3), "throughput_solves_s": round(solves_done / wall, 3),
+            "max_true_resid": max([d[6] for d in done], default=None),
+            "config": {"lattices": SERVE_LATTICES, "Ns": [8, 16], "mq": [0.002, 0.5], "nrhs": [1, 12],
+                       "prec": args.prec, "tol": TOL, "arrivals": "Poisson, seed 21"}}
+    print(json.dumps(line), flush=True)
+    srv.close()
+
+
+C3_DIMS = (24, 24, 24, 48)
+C5_DIMS = (64, 64, 64, 64)
+
+
+def _solve_stats_line(stats):
+    return {"iters": [s["iters"] for s in stats], "reliable_updates": [s["n_reliable"] for s in stats],
+            "max_true_resid": max(s["true_resid"] for s in stats)}
+
+
+def run_batched_c3(args, world, rank, local):
+    """24^3 x 48 x Ns=16: 12 point sources (every spin-colour component at one seeded even
+    site, wall placement) x 3 masses = 36 systems in one batched mixed-precision call; links
+    exp(0.25 i H) seed 3.  The right-hand sides are shared by the three masses of a source.
+    Prints solves/s of the batched call, the per-system iteration counts, and the FP64 GPU CG
+    on one source's three systems for comparison."""
+    import torch
+
+    import odwf_synth as syn
+    import paper_1811_08095_gb300 as odwf
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    dims = C3_DIMS
+    vh = dims[0] * dims[1] * dims[2] * dims[3] // 2
+    w, _ = odwf.odwf_zolotarev_omega(NS, LRANGE[0], LRANGE[1])
+    U = syn.gauge_field_torch(dims, EPS, 3, device=dev)
+    h = odwf.Handle(dims, NS, M0, MASSES[0], w)
+    h.set_gauge(U)
+    del U
+    site, idx = syn.random_even_site(dims, 7)
+    srcs = []
+    for sc in range(12):
+        spin, col = divmod(sc, 3)
+        b = torch.zeros((NS, vh, 4, 3), dtype=torch.complex128, device=dev)
+        b[NS - 1 if spin < 2 else 0, idx, spin, col] = 1.0
+        srcs.append(b)
+    bs = [srcs[k] for k in range(12) for _ in MASSES]
+    mqs = [m for _ in range(12) for m in MASSES]
+    xs = [torch.zeros_like(srcs[0]) for _ in bs]
+    torch.cuda.synchronize()
+
+    def step(prec, xs_, bs_, mqs_):
+        return h.cg_solve_batched(xs_, bs_, mqs_, tol=TOL, max_iter=200000, prec=prec, delta=args.delta,
+                                  link_recon=args.link_recon, stream=stream)
+
+    for _ in range(args.warmup):
+        step(args.prec, xs, bs, mqs)
+    torch.cuda.synchronize()
+    launches0 = odwf.load().odwf_launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, stats = [], None
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats = step(args.prec, xs, bs, mqs)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    clk = clocks.stop()
+    launches = odwf.load().odwf_launch_count() - launches0
+    for s in stats:
+        assert s["status"] == 0 and s["true_resid"] <= TOL, s
+    mem = torch.cuda.max_memory_allocated(dev)
+    free, total = torch.cuda.mem_get_info(dev)
+    fp64 = None
+    if not args.skip_fp64:
+        x3 = xs[:3]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st64 = step("f64", x3, bs[:3], mqs[:3])
+        e1.record(stream)
+        e1.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        fp64 = {"value": round(3 / t64, 4), "unit": "solves/s", "systems": "source 0 x 3 masses",
+                **_solve_stats_line(st64)}
+    value = len(bs) / (sum(times) / len(times))
+    line = {"metric": METRIC, "workload": "odwf_dagd_24x24x24x48_ns16_12src_3mass_batched", "value": round(value, 4),
+            "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "s_per_step": round(sum(times) / len(times), 3), "systems": len(bs), "dtype": "f32",
+            "data": "synthetic", **_solve_stats_line(stats), "fp64_cg_subset": fp64,
+            "gpu_launches": int(launches), "clocks": clk,
+            "device_memory": {"torch_allocated_peak_gb": round(mem / 1e9, 2),
+                              "used_gb_at_end": round((total - free) / 1e9, 2), "total_gb": round(total / 1e9, 2)},
+            "config": {"lattice": "24^3x48", "Ns": NS, "m0": M0, "masses": list(MASSES),
+                       "sources": "12 spin-colour point sources at even site %s, wall placement" % (site,),
+                       "gauge": "U = exp(0.25 i H) (seed 3)", "prec": args.prec, "link_recon": args.link_recon,
+                       "delta": args.delta, "tol": TOL, "omega": "shifted (R5) Zolotarev on [0.05, 6.2]"}}
+    print(json.dumps(line), flush=True)
+    h.close()
+
+
+def run_paper_scale_c5(args, world, rank, local):
+    """64^4 x Ns=16, m_q = 0.002, links exp(0.2 i H) seed 5 stored as FP32 12-real, BF16 inner
+    solve with FP64 reliable updates, one Gaussian right-hand side (seed 5), one solve per
+    step.  Reports the solve time, iterations, true residual and the device memory used."""
+    import torch
+
+    import odwf_synth as syn
+    import paper_1811_08095_gb300 as odwf
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    dims = C5_DIMS
+    vh = dims[0] * dims[1] * dims[2] * dims[3] // 2
+    mq = 0.002
+    w, _ = odwf.odwf_zolotarev_omega(NS, LRANGE[0], LRANGE[1])
+    U = syn.gauge_field_torch(dims, 0.2, 5, device=dev)
+    h = odwf.Handle(dims, NS, M0, mq, w)
+    h.set_gauge(U)
+    del U
+    torch.cuda.empty_cache()
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    b = torch.randn((NS, vh, 4, 3), dtype=torch.complex128, device=dev, generator=g)
+    x = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    prec = "bf16" if args.prec == "f16" else args.prec
+    times, st = [], None
+    for i in range(args.warmup + args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        clocks = ClockSampler(local)
+        if i >= args.warmup:
+            clocks.start()
+        e0.record(stream)
+        st = h.cg_solve(x, b, tol=TOL, max_iter=200000, prec=prec, delta=args.delta, link_recon=12, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= args.warmup:
+            times.append(e0.elapsed_time(e1) / 1e3)
+            clk = clocks.stop()
+    assert st["status"] == 0 and st["true_resid"] <= TOL, st
+    free, total = torch.cuda.mem_get_info(dev)
+    line = {"metric": METRIC, "workload": "odwf_dagd_64x64x64x64_ns16_single", "value": round(1 / (sum(times) /
+            len(times)), 5), "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "s_per_solve": round(sum(times) / len(times), 2), "iters": st["iters"], "reliable_updates":
+            st["n_reliable"], "true_resid": st["true_resid"], "dtype": "f32", "data": "synthetic", "clocks": clk,
+            "device_memory": {"used_gb": round((total - free) / 1e9, 2), "total_gb": round(total / 1e9, 2)},
+            "config": {"lattice": "64^4", "Ns": NS, "m0": M0, "mq": mq, "gauge": "U = exp(0.2 i H) (seed 5)",
+                       "links": "FP32, 12 reals", "prec": prec, "delta": args.delta, "tol": TOL,
+                       "rhs": "unit Gaussian (torch seed 5)"}}
+    print(json.dumps(line), flush=True)
+    h.close()
+
+
 def run_reference(args, world, rank, local):
     """The oracle (FP64 CPU program) on host cores: each step is one oracle CG iteration on the
     workload, scaled to solves/s by the oracle's own iteration counts (tests/golden)."""
@@ -383,12 +611,23 @@ def main():
     ap.add_argument("--prec", default="f16", choices=["f16", "bf16", "f32"])
     ap.add_argument("--delta", type=float, default=0.01, help="reliable-update threshold")
     ap.add_argument("--link-recon", type=int, default=12, choices=[12, 18])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "serve"],
+                    help="c2: the default line; c3: 36-system batch on 24^3x48; c5: one 64^4 solve; serve")
+    ap.add_argument("--rate", type=float, default=50.0, help="serve: arrivals per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
+    ap.add_argument("--drain", type=float, default=60.0, help="serve: extra seconds to finish pending requests")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, world, rank, local)
+    elif args.workload == "serve":
+        run_serve(args, world, rank, local)
+    elif args.workload == "c3":
+        run_batched_c3(args, world, rank, local)
+    elif args.workload == "c5":
+        run_paper_scale_c5(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 

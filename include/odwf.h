@@ -266,8 +266,10 @@ typedef struct {
     double mq;
     const double* omega;  /* host, Ns doubles; copied at submit */
     int32_t nrhs;
-    const void* const* b; /* nrhs host or device pointers, SCHUR_EVEN layout */
-    void* const* x;       /* nrhs output pointers, same kind as b */
+    const void* const* b; /* nrhs host or device pointers, SCHUR_EVEN layout; a device b is
+                             read again during the solve and must stay valid (and unchanged)
+                             until the request completes; host data is copied at admission */
+    void* const* x;       /* nrhs output pointers, same kind as b, written at completion */
     double tol;
     int32_t prec;         /* inner precision, as odwf_solve_params.prec */
     int32_t max_iter;

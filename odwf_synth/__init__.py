@@ -28,7 +28,7 @@ import numpy as np
 
 __all__ = [
     "gell_mann", "gauge_field", "gauge_field_torch", "gaussian_spinor",
-    "gaussian_spinor_even", "point_source", "random_site", "volume",
+    "gaussian_spinor_even", "point_source", "random_site", "random_even_site", "volume",
     "even_sites",
 ]
 
@@ -79,7 +79,7 @@ def gauge_field(dims, eps: float, seed: int, chunk: int = 1 << 20) -> np.ndarray
 
 
 def gauge_field_torch(dims, eps: float, seed: int, device="cuda"):
-    """Same recipe on a torch device (for lattices where the host path is slow)."""
+    """Same distribution on a torch device (for lattices where the host path is slow)."""
     import torch
 
     lx, ly, lz, lt = dims
@@ -93,9 +93,8 @@ def gauge_field_torch(dims, eps: float, seed: int, device="cuda"):
         i1 = min(n, i0 + chunk)
         h = torch.randn((i1 - i0, 8), generator=g, device=device, dtype=torch.float64)
         hm = torch.einsum("na,aij->nij", h.to(torch.complex128), lam)
-        w, v = torch.linalg.eigh(hm)
-        ph = torch.exp(1j * eps * w.to(torch.complex128))
-        out[i0:i1] = torch.einsum("nab,nb,ncb->nac", v, ph, v.conj())
+        # matrix exponential by scaling and squaring (no batched eigensolver needed on the device)
+        out[i0:i1] = torch.linalg.matrix_exp(1j * eps * hm)
     return out.reshape(4, lt, lz, ly, lx, 3, 3)
 
 
@@ -127,6 +126,17 @@ def even_sites(dims) -> np.ndarray:
 def random_site(dims, seed: int):
     rng = np.random.default_rng(seed)
     return tuple(int(rng.integers(0, L)) for L in dims)
+
+
+def random_even_site(dims, seed: int):
+    """A seeded site with x + y + z + t even, and its index among the even sites."""
+    lx, ly, lz, lt = dims
+    rng = np.random.default_rng(seed)
+    while True:
+        site = tuple(int(rng.integers(0, L)) for L in dims)
+        if sum(site) % 2 == 0:
+            x, y, z, t = site
+            return site, (((t * lz + z) * ly + y) * lx + x) // 2
 
 
 def point_source(ns: int, dims, site, spin: int, color: int) -> np.ndarray:

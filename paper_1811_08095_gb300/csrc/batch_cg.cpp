@@ -7,6 +7,11 @@
 namespace odwf {
 
 BatchCG::~BatchCG() {
+    if (s_rel) cudaStreamSynchronize(s_rel);
+    for (cudaEvent_t e : ev_rel)
+        if (e) cudaEventDestroy(e);
+    if (s_rel) cudaStreamDestroy(s_rel);
+    if (ev_sync) cudaEventDestroy(ev_sync);
     if (st_host) cudaFreeHost(st_host);
 }
 
@@ -39,8 +44,9 @@ int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStr
     tol = prm.tol;
     max_iter = prm.max_iter;
     int rc = 0;
-    if ((rc = E->alloc_half("cg.X64", Sp::F64, cap, &X64)) || (rc = E->alloc_half("cg.R64", Sp::F64, cap, &R64)) ||
-        (rc = E->alloc_half("cg.B64", Sp::F64, cap, &B64)))
+    const int nrb = mixed ? 1 : cap;  // mixed: R64 and B64 are shared by all systems
+    if ((rc = E->alloc_half("cg.X64", Sp::F64, cap, &X64)) || (rc = E->alloc_half("cg.R64", Sp::F64, nrb, &R64)) ||
+        (rc = E->alloc_half("cg.B64", Sp::F64, nrb, &B64)))
         return rc;
     if (!mixed) {
         if ((rc = E->alloc_half("cg.P64", Sp::F64, cap, &P64)) || (rc = E->alloc_half("cg.T64", Sp::F64, cap, &T64)) ||
@@ -78,6 +84,12 @@ int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStr
     ODWF_CK(cudaMemcpyAsync(st, st_host, sizeof(SysState) * cap, cudaMemcpyHostToDevice, s));
     ODWF_CK(cudaStreamSynchronize(s));
     n_reliable.assign(cap, 0);
+    upd.assign(cap, 0);
+    ODWF_CK(cudaStreamCreateWithFlags(&s_rel, cudaStreamNonBlocking));
+    ODWF_CK(cudaEventCreateWithFlags(&ev_sync, cudaEventDisableTiming));
+    bsrc.assign(cap, nullptr);
+    ev_rel.assign(cap, nullptr);
+    for (int i = 0; i < cap; ++i) ODWF_CK(cudaEventCreateWithFlags(&ev_rel[i], cudaEventDisableTiming));
     active.assign(cap, 0);
     mq.assign(cap, 0.0);
     slot_tol.assign(cap, tol);
@@ -114,14 +126,45 @@ int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStr
 int BatchCG::admit(int slot, const double2* b_ext, double mq_slot, cudaStream_t s, double tol_slot,
                    int max_iter_slot) {
     if (slot < 0 || slot >= cap) return fail(ODWF_EINVAL, "admit: bad slot");
-    ODWF_CK(launch_pack(Sp::F64, b_ext, B64.ref_sys(slot), E->g, 0, E->ns, 1, s));
     mq[slot] = mq_slot;
-    return admit_internal(slot, s, tol_slot, max_iter_slot);
+    const size_t eb = E->sites5() * 12 * sizeof(double2);
+    const double2* bd = b_ext;
+    if (!is_device_ptr(b_ext)) {
+        // mixed: one copy per slot (read again at every update); FP64: packed at once, one buffer
+        int rc = 0;
+        bstage = (double2*)E->get_ws("cg.bstage", eb * (mixed ? cap : 1), &rc);
+        if (rc) return rc;
+        double2* dst = (double2*)((char*)bstage + eb * (mixed ? slot : 0));
+        ODWF_CK(cudaMemcpyAsync(dst, b_ext, eb, cudaMemcpyHostToDevice, s));
+        bd = dst;
+    }
+    if (!mixed) {
+        ODWF_CK(launch_pack(Sp::F64, bd, B64.ref_sys(slot), E->g, 0, E->ns, 1, s));
+        return admit_internal(slot, s, tol_slot, max_iter_slot);
+    }
+    bsrc[slot] = bd;
+    int rc = order_after(s_rel, s);  // the shared FP64 buffers are free
+    if (!rc) rc = load_b(slot, s);
+    if (!rc) rc = admit_internal(slot, s, tol_slot, max_iter_slot);
+    if (!rc) rc = order_after(s, s_rel);  // later updates start after this admission's reads
+    return rc;
+}
+
+int BatchCG::order_after(cudaStream_t first, cudaStream_t then) {
+    ODWF_CK(cudaEventRecord(ev_sync, first));
+    ODWF_CK(cudaStreamWaitEvent(then, ev_sync, 0));
+    return ODWF_OK;
+}
+
+int BatchCG::load_b(int slot, cudaStream_t s) {
+    if (mixed && bsrc[slot]) ODWF_CK(launch_pack(Sp::F64, bsrc[slot], B64.ref_sys(0), E->g, 0, E->ns, 1, s));
+    return ODWF_OK;
 }
 
 int BatchCG::release(int slot) {
     if (slot < 0 || slot >= cap) return fail(ODWF_EINVAL, "release: bad slot");
     active[slot] = 0;
+    if (!bsrc.empty()) bsrc[slot] = nullptr;
     st_host[slot].status = kIdle;
     return ODWF_OK;
 }
@@ -145,22 +188,21 @@ int BatchCG::admit_internal(int slot, cudaStream_t s, double tol_slot, int max_i
     *stage = init;
     ODWF_CK(cudaMemcpyAsync(st + slot, stage, sizeof(SysState), cudaMemcpyHostToDevice, s));
     // ||b||^2 -> state, then rr = bb, status running
-    ODWF_CK(launch_vec(Sp::F64, Sp::F64, B64.ref(), B64.ref(), n5, ns, 3, 0.0, st, 0, 0, partials, counters, slot,
-                       1, s));
+    const FieldRef B = Bref();
+    ODWF_CK(launch_vec(Sp::F64, Sp::F64, B, B, n5, ns, 3, 0.0, st, 0, 0, partials, counters, slot, 1, s));
     ODWF_CK(launch_state(st + slot, 1, 0, tl * tl, s));
     ODWF_CK(launch_vec(Sp::F64, Sp::F64, X64.ref(), X64.ref(), n5, ns, 5, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
-    ODWF_CK(launch_vec(Sp::F64, Sp::F64, B64.ref(), R64.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
     if (!mixed) {
-        ODWF_CK(launch_vec(Sp::F64, Sp::F64, B64.ref(), P64.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
+        ODWF_CK(launch_vec(Sp::F64, Sp::F64, B, R64.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
+        ODWF_CK(launch_vec(Sp::F64, Sp::F64, B, P64.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
     } else {
-        ODWF_CK(launch_vec(Sp::F64, Sp::F32, B64.ref(), Rin.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
+        ODWF_CK(launch_vec(Sp::F64, Sp::F32, B, Rin.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
         ODWF_CK(launch_vec(Sp::F32, Sp::F32, Xin.ref(), Xin.ref(), n5, ns, 5, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
         if (v2) {
             ODWF_CK(launch_p_update2(low, ns, Rin.ref(), Pl.ref(), Chil.ref(), E->vh(), 0, E->cf32, r_dev, st, 0, 0,
                                      slot, 1, nullptr, s));
         } else {
-            ODWF_CK(launch_vec(Sp::F64, low, B64.ref(), Pl.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1,
-                               s));
+            ODWF_CK(launch_vec(Sp::F64, low, B, Pl.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
         }
     }
     active[slot] = 1;
@@ -306,15 +348,40 @@ bool BatchCG::slot_finished(int i) const {
 
 int BatchCG::any_running() const {
     for (int i = 0; i < cap; ++i)
-        if (active[i] && slot_running(i)) return 1;
+        if (active[i] && (slot_running(i) || upd[i])) return 1;
     return 0;
 }
 
-// R[slot] = B[slot] - S^dag S X[slot] in FP64, |R|^2 -> st[slot].sum
-int BatchCG::fp64_residual(int slot, const HalfField& X, const HalfField& R, cudaStream_t s) {
+int BatchCG::resume(cudaStream_t s, bool block) {
+    bool any_iterating = false;
+    for (int i = 0; i < cap; ++i)
+        if (active[i] && !upd[i] && st_host[i].status == kRunning) any_iterating = true;
+    for (int i = 0; i < cap; ++i) {
+        if (!upd[i]) continue;
+        cudaError_t q = cudaEventQuery(ev_rel[i]);
+        if (q == cudaErrorNotReady && block && !any_iterating) {
+            ODWF_CK(cudaEventSynchronize(ev_rel[i]));  // nothing else to do: wait for this update
+            q = cudaSuccess;
+        }
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) return cuda_fail(q, "cudaEventQuery(reliable update)");
+        // the iteration stream waits for the update, then the slot rejoins (kRestarting -> kRunning)
+        ODWF_CK(cudaStreamWaitEvent(s, ev_rel[i], 0));
+        ODWF_CK(launch_state(st + i, 1, 2, 0.0, s));
+        upd[i] = 0;
+        st_host[i].status = kRunning;  // host view until the next poll
+        any_iterating = true;
+    }
+    return ODWF_OK;
+}
+
+// R[slot] = B[slot] - S^dag S X[slot] in FP64, |R|^2 -> st[slot].sum (mixed: R and B are the
+// shared buffers, B loaded with the slot's right-hand side)
+int BatchCG::fp64_residual(int slot, cudaStream_t s) {
+    const HalfField& X = X64;
     FieldRef t, a, c;
     if (mixed) {
-        t = R.ref();  // R[slot] is rewritten by the last hop; it holds t = M^-1 H_oe x until then
+        t = Rref();  // R is rewritten by the last hop; it holds t = M^-1 H_oe x until then
         a = A1.ref_shared();
         c = C1.ref_shared();
     } else {
@@ -340,8 +407,8 @@ int BatchCG::fp64_residual(int slot, const HalfField& X, const HalfField& R, cud
     P.p_out = 0;
     P.in = c;
     P.z = a;
-    P.b = B64.ref();
-    P.out = R.ref();
+    P.b = Bref();
+    P.out = Rref();
     { auto pb_ = prof_begin(pcls_rel[3], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_f64(P, Epi::D_NORMAL_RESID, 1, s)); prof_end(pb_, s); P.prof_count = nullptr; }
     return ODWF_OK;
 }
@@ -349,43 +416,59 @@ int BatchCG::fp64_residual(int slot, const HalfField& X, const HalfField& R, cud
 int BatchCG::service(cudaStream_t s) {
     const size_t n5 = E->sites5();
     for (int i = 0; i < cap; ++i) {
-        if (!active[i] || st_host[i].status != kNeedUpdate) continue;
+        if (!active[i] || upd[i] || st_host[i].status != kNeedUpdate) continue;
+        // the update stream starts after this slot's last iteration on s
+        ODWF_CK(cudaEventRecord(ev_rel[i], s));
+        ODWF_CK(cudaStreamWaitEvent(s_rel, ev_rel[i], 0));
+        cudaStream_t r = s_rel;
         if (mixed)  // X64 += x_in, x_in = 0
             ODWF_CK(launch_vec(Sp::F32, Sp::F64, Xin.ref(), X64.ref(), n5, E->ns, 2, 0.0, st, 0, 0, nullptr, nullptr,
-                               i, 1, s));
-        int rc = fp64_residual(i, X64, R64, s);
+                               i, 1, r));
+        int rc = load_b(i, r);
+        if (!rc) rc = fp64_residual(i, r);
         if (rc) return rc;
-        ODWF_CK(launch_state(st + i, 1, 1, tol * tol, s));
+        ODWF_CK(launch_state(st + i, 1, 1, tol * tol, r));  // done / max-iter / kRestarting
         if (mixed) {
-            ODWF_CK(launch_vec(Sp::F64, Sp::F32, R64.ref(), Rin.ref(), n5, E->ns, 0, 0.0, st, 1, kRunning, nullptr,
-                               nullptr, i, 1, s));
+            ODWF_CK(launch_vec(Sp::F64, Sp::F32, Rref(), Rin.ref(), n5, E->ns, 0, 0.0, st, 1, kRestarting, nullptr,
+                               nullptr, i, 1, r));
             if (v2) {
                 ODWF_CK(launch_p_update2(low, E->ns, Rin.ref(), Pl.ref(), Chil.ref(), E->vh(), 1, E->cf32, r_dev, st,
-                                         1, kRunning, i, 1, nullptr, s));
+                                         1, kRestarting, i, 1, nullptr, r));
             } else {
-                ODWF_CK(launch_vec(Sp::F32, low, Rin.ref(), Pl.ref(), n5, E->ns, 1, 0.0, st, 1, kRunning, nullptr,
-                                   nullptr, i, 1, s));
+                ODWF_CK(launch_vec(Sp::F32, low, Rin.ref(), Pl.ref(), n5, E->ns, 1, 0.0, st, 1, kRestarting, nullptr,
+                                   nullptr, i, 1, r));
             }
         } else {
-            ODWF_CK(launch_vec(Sp::F64, Sp::F64, R64.ref(), P64.ref(), n5, E->ns, 1, 0.0, st, 1, kRunning, nullptr,
-                               nullptr, i, 1, s));
+            ODWF_CK(launch_vec(Sp::F64, Sp::F64, R64.ref(), P64.ref(), n5, E->ns, 1, 0.0, st, 1, kRestarting, nullptr,
+                               nullptr, i, 1, r));
         }
+        ODWF_CK(cudaEventRecord(ev_rel[i], r));
+        upd[i] = 1;
         n_reliable[i] += 1;
-        st_host[i].status = kRunning;  // host view until the next poll
+        st_host[i].status = kRestarting;  // host view until the next poll
     }
     return ODWF_OK;
 }
 
 int BatchCG::finalize(int slot, double2* x_ext, cudaStream_t s, double* true_resid) {
+    if (upd[slot]) {
+        ODWF_CK(cudaStreamWaitEvent(s, ev_rel[slot], 0));
+        upd[slot] = 0;
+    }
     ODWF_CK(cudaMemcpyAsync(st_host + slot, st + slot, sizeof(SysState), cudaMemcpyDeviceToHost, s));
     ODWF_CK(cudaStreamSynchronize(s));
     const int stt = st_host[slot].status;
     if (stt != kDone && stt != kMaxIter) {
         // breakdown (or an unfinished slot): fold and recompute the true residual
-        if (mixed)
+        int rc = ODWF_OK;
+        if (mixed) {
             ODWF_CK(launch_vec(Sp::F32, Sp::F64, Xin.ref(), X64.ref(), E->sites5(), E->ns, 2, 0.0, st, 0, 0, nullptr,
                                nullptr, slot, 1, s));
-        int rc = fp64_residual(slot, X64, R64, s);
+            rc = order_after(s_rel, s);  // the shared FP64 buffers are free
+            if (!rc) rc = load_b(slot, s);
+        }
+        if (!rc) rc = fp64_residual(slot, s);
+        if (!rc && mixed) rc = order_after(s, s_rel);
         if (rc) return rc;
     }
     if (x_ext) ODWF_CK(launch_unpack(Sp::F64, X64.ref_sys(slot), x_ext, E->g, 0, E->ns, 1, s));

@@ -14,6 +14,14 @@
 // largest value since the last update (or below the target) is parked; the host then
 // folds x into the FP64 solution, recomputes r = b - S^dag S x in FP64 on the GPU and
 // restarts the inner iteration from it (reliable updates).
+//
+// Memory (mixed precision): per system the FP64 solution, the FP32 inner r and x and the
+// five low-precision operator fields.  The FP64 right-hand side is not copied per system:
+// the caller's b (external layout) is re-packed into one shared FP64 buffer at every
+// reliable update, and the FP64 residual lives in a second shared buffer.  Updates run
+// one after another on the update stream, and admissions / final checks on the iteration
+// stream are ordered against that stream, so the shared buffers are never used by two
+// systems at once.
 #pragma once
 
 #include <chrono>
@@ -34,7 +42,7 @@ struct BatchCG {
     double tol = 1e-10;
     int max_iter = 10000;
 
-    // per-slot fields (slabs of `cap`)
+    // per-slot fields (slabs of `cap`); in mixed mode R64 and B64 are one shared system
     HalfField X64, R64, B64;       // FP64 solution, residual, right-hand side
     HalfField P64, T64, A64, C64;  // FP64 CG (mixed = false) operator fields
     HalfField Rin, Xin;            // mixed: FP32 inner residual / solution
@@ -48,8 +56,15 @@ struct BatchCG {
     double* r_dev = nullptr;       // device [cap]
     double* partials = nullptr;    // device [cap * nblk]
     unsigned* counters = nullptr;  // device [cap]
+    // reliable updates run on their own stream, overlapping the other systems' iterations
+    cudaStream_t s_rel = nullptr;
+    std::vector<cudaEvent_t> ev_rel;  // per slot: end of its update on s_rel
+    std::vector<int> upd;             // per slot: an update is in flight
     std::vector<int> n_reliable;
     std::vector<int> active;       // host view: slot holds a system
+    std::vector<const double2*> bsrc;  // mixed: the slot's right-hand side (device, external layout)
+    double2* bstage = nullptr;         // mixed: per-slot device copies of host right-hand sides [cap]
+    cudaEvent_t ev_sync = nullptr;     // orders the shared FP64 buffers between the two streams
     std::vector<double> mq;
     std::vector<double> slot_tol;
     int pcls[5] = {-1, -1, -1, -1, -1};  // profiler classes: K1..K4, p update
@@ -57,13 +72,15 @@ struct BatchCG {
 
     ~BatchCG();
     int init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStream_t s);
-    // b_ext: device pointer to an even-site external field (complex128)
-    // tol_slot / max_iter_slot <= 0 keep the batch defaults
+    // b_ext: even-site external field (complex128).  A device pointer is read again at every
+    // reliable update (mixed precision) and must stay valid until finalize(); a host pointer is
+    // copied.  tol_slot / max_iter_slot <= 0 keep the batch defaults.
     int admit(int slot, const double2* b_ext, double mq_slot, cudaStream_t s, double tol_slot = 0,
               int max_iter_slot = 0);
     int admit_internal(int slot, cudaStream_t s, double tol_slot = 0, int max_iter_slot = 0);  // B64[slot] filled
     int release(int slot);  // slot free for the next admit
     int run_iterations(int k, cudaStream_t s);
+    int resume(cudaStream_t s, bool block);          // rejoin slots whose update finished
     int poll(cudaStream_t s);                      // refresh st_host (synchronizes s)
     int service(cudaStream_t s);                   // reliable updates for parked slots
     int finalize(int slot, double2* x_ext, cudaStream_t s, double* true_resid);
@@ -74,7 +91,11 @@ struct BatchCG {
    private:
     template <class R>
     HopParams<R> params(int p_out) const;
-    int fp64_residual(int slot, const HalfField& X, const HalfField& R, cudaStream_t s);
+    int fp64_residual(int slot, cudaStream_t s);
+    FieldRef Rref() const { return mixed ? R64.ref_shared() : R64.ref(); }
+    FieldRef Bref() const { return mixed ? B64.ref_shared() : B64.ref(); }
+    int load_b(int slot, cudaStream_t s);               // mixed: pack the slot's b into the shared B64
+    int order_after(cudaStream_t first, cudaStream_t then);  // `then` waits for work queued on `first`
 };
 
 }  // namespace odwf

@@ -483,12 +483,11 @@ int Engine::solve(int nsys, void* const* x, const void* const* b, const double* 
         double m = mq;
         if (mq_arr) m = mq_arr[i];
         else if (std::isfinite(prm->mq)) m = prm->mq;
-        const double2* db = nullptr;
-        if ((rc = stage_in(this, b[i], eb, "ext.in", st, &db))) return rc;
-        if ((rc = bc.admit(i, db, m, st))) return rc;
+        if ((rc = bc.admit(i, (const double2*)b[i], m, st))) return rc;
     }
     const int every = prm->check_every > 0 ? prm->check_every : 8;
     while (true) {
+        if ((rc = bc.resume(st, true))) return rc;
         if ((rc = bc.run_iterations(every, st))) return rc;
         if ((rc = bc.poll(st))) return rc;
         if ((rc = bc.service(st))) return rc;

@@ -26,6 +26,7 @@ int run_cg(BatchCG& bc, double mqv, cudaStream_t st, int every, int* iters, int*
     bc.mq[0] = mqv;
     if ((rc = bc.admit_internal(0, st))) return rc;
     while (true) {
+        if ((rc = bc.resume(st, true))) return rc;
         if ((rc = bc.run_iterations(every, st))) return rc;
         if ((rc = bc.poll(st))) return rc;
         if ((rc = bc.service(st))) return rc;

@@ -140,7 +140,8 @@ cudaError_t launch_vec(Sp spx, Sp spy, const FieldRef& x, const FieldRef& y, siz
 // One thread per system: CG bookkeeping between phases.
 //   mode 0 (init):  rr = bb = sum, r_max = sqrt(sum), status running (done when b = 0)
 //   mode 1 (after a reliable update, sum = ||b - A x||^2): done / max-iter / restart with
-//                   beta = sum / rr_prev, rr = sum, r_max = sqrt(sum)
+//                   beta = sum / rr_prev, rr = sum, r_max = sqrt(sum) (status kRestarting)
+//   mode 2:         kRestarting -> kRunning (launched on the iteration stream)
 __global__ void state_kernel(SysState* st, int nsys, int mode, double tol2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nsys) return;
@@ -153,6 +154,8 @@ __global__ void state_kernel(SysState* st, int nsys, int mode, double tol2) {
         S.iter = 0;
         S.alpha = S.beta = 0.0;
         S.status = (S.sum > 0.0) ? kRunning : kDone;
+    } else if (mode == 2) {
+        if (S.status == kRestarting) S.status = kRunning;
     } else {
         if (S.status != kNeedUpdate) return;
         const double rt = S.sum;
@@ -168,7 +171,7 @@ __global__ void state_kernel(SysState* st, int nsys, int mode, double tol2) {
             S.beta = rt / S.rr;
             S.rr = rt;
             S.r_max = sqrt(rt);
-            S.status = kRunning;
+            S.status = kRestarting;
         }
     }
 }

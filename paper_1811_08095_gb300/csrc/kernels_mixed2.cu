@@ -14,6 +14,8 @@
 // warp, so a warp barrier suffices).  The per-site FP16/BF16 scale and the time-boundary
 // sign of each neighbour are folded into the FMAs that accumulate its contribution.  Ns
 // is a template parameter, so the fifth-dimension scans unroll.
+#include <type_traits>
+
 #include "kernels.cuh"
 #include "kernels.h"
 
@@ -103,65 +105,67 @@ __device__ __forceinline__ void project_raw(int mu, float sg, const float v[24],
 // arithmetic uses the FP32x2 FMA of sm_100+ (one instruction for two lanes of work).
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// Load one 5D site as spin pairs: up half (spins 0, 1) and down half (spins 2, 3; in the
-// order (3, 2) when SWAP_DN).  Returns the site's scale.
-template <class SP, bool SWAP_DN>
-struct PackedLoad;
+// Raw stored words of one 5D site (fetched ahead of use so that the next neighbour's loads
+// are in flight while the current one is processed) and their unpacking into spin pairs:
+// up half (spins 0, 1) and down half (spins 2, 3; in the order (3, 2) when SWAP_DN).
+template <class SP>
+struct RawSite;
+template <>
+struct RawSite<SpF16> { uint4 q[3]; float sc; };
+template <>
+struct RawSite<SpBF16> { uint4 q[3]; float sc; };
+template <>
+struct RawSite<SpF32> { float4 q[6]; float sc; };
 
-template <class H2, bool SWAP_DN>
-struct PackedHalfLoad {
-    static __device__ __forceinline__ float load(const void* base, const float* norm, size_t h, int s, int ns,
-                                                 float2 Ur[3], float2 Ui[3], float2 Dr[3], float2 Di[3]) {
+template <class SP>
+__device__ __forceinline__ void fetch_site(const void* base, const float* norm, size_t h, int s, int ns, bool valid,
+                                           RawSite<SP>& r) {
+    if (std::is_same<SP, SpF32>::value) {
+        const float4* p = reinterpret_cast<const float4*>(base);
+        float4* q = reinterpret_cast<float4*>(&r);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) q[k] = valid ? __ldg(p + chunk_off(h, k, 6, ns, s)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        r.sc = 1.f;
+    } else {
         const uint4* p = reinterpret_cast<const uint4*>(base);
-        const float sc = __ldg(norm + h * ns + s);
-        float2 f[12];  // word w = (spin w/3, colour w%3): (re, im)
+        uint4* q = reinterpret_cast<uint4*>(&r);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const uint4 q = __ldg(p + chunk_off(h, k, 3, ns, s));
-            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                H2 hv;
-                *reinterpret_cast<uint32_t*>(&hv) = w[j];
-                f[4 * k + j] = Half2Cvt<H2>::to_f2(hv);
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            Ur[c] = make_float2(f[c].x, f[3 + c].x);
-            Ui[c] = make_float2(f[c].y, f[3 + c].y);
-            if (SWAP_DN) {
-                Dr[c] = make_float2(f[9 + c].x, f[6 + c].x);
-                Di[c] = make_float2(f[9 + c].y, f[6 + c].y);
-            } else {
-                Dr[c] = make_float2(f[6 + c].x, f[9 + c].x);
-                Di[c] = make_float2(f[6 + c].y, f[9 + c].y);
-            }
-        }
-        return sc;
+        for (int k = 0; k < 3; ++k) q[k] = valid ? __ldg(p + chunk_off(h, k, 3, ns, s)) : make_uint4(0u, 0u, 0u, 0u);
+        r.sc = valid ? __ldg(norm + h * ns + s) : 0.f;
     }
-};
-template <bool SW>
-struct PackedLoad<SpF16, SW> : PackedHalfLoad<__half2, SW> {};
-template <bool SW>
-struct PackedLoad<SpBF16, SW> : PackedHalfLoad<__nv_bfloat162, SW> {};
-template <bool SWAP_DN>
-struct PackedLoad<SpF32, SWAP_DN> {
-    static __device__ __forceinline__ float load(const void* base, const float*, size_t h, int s, int ns,
-                                                 float2 Ur[3], float2 Ui[3], float2 Dr[3], float2 Di[3]) {
-        float v[24];
-        RawIO<SpF32>::load(base, nullptr, h, s, ns, v);
+}
+
+template <class SP, bool SWAP_DN>
+__device__ __forceinline__ void unpack_site(const RawSite<SP>& r, float2 Ur[3], float2 Ui[3], float2 Dr[3],
+                                            float2 Di[3]) {
+    float2 f[12];  // word w = (spin w/3, colour w%3): (re, im)
+    if (std::is_same<SP, SpF32>::value) {
+        const float* v = reinterpret_cast<const float*>(&r);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            Ur[c] = make_float2(v[2 * c], v[6 + 2 * c]);
-            Ui[c] = make_float2(v[2 * c + 1], v[6 + 2 * c + 1]);
-            const int a = SWAP_DN ? 18 : 12, b = SWAP_DN ? 12 : 18;
-            Dr[c] = make_float2(v[a + 2 * c], v[b + 2 * c]);
-            Di[c] = make_float2(v[a + 2 * c + 1], v[b + 2 * c + 1]);
+        for (int w = 0; w < 12; ++w) f[w] = make_float2(v[2 * w], v[2 * w + 1]);
+    } else {
+        using H2 = typename std::conditional<std::is_same<SP, SpF16>::value, __half2, __nv_bfloat162>::type;
+        const uint32_t* wd = reinterpret_cast<const uint32_t*>(&r);
+#pragma unroll
+        for (int w = 0; w < 12; ++w) {
+            H2 hv;
+            *reinterpret_cast<uint32_t*>(&hv) = wd[w];
+            f[w] = Half2Cvt<H2>::to_f2(hv);
         }
-        return 1.f;
     }
-};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        Ur[c] = make_float2(f[c].x, f[3 + c].x);
+        Ui[c] = make_float2(f[c].y, f[3 + c].y);
+        if (SWAP_DN) {
+            Dr[c] = make_float2(f[9 + c].x, f[6 + c].x);
+            Di[c] = make_float2(f[9 + c].y, f[6 + c].y);
+        } else {
+            Dr[c] = make_float2(f[6 + c].x, f[9 + c].x);
+            Di[c] = make_float2(f[6 + c].y, f[9 + c].y);
+        }
+    }
+}
 
 // One hop direction in spin pairs.  H = v^up + sg G v^dn (G of gamma_mu in the chiral basis,
 // gamma_mu = [[0, G], [G^dag, 0]]); W = U H (or U^dag H); then
@@ -169,21 +173,31 @@ struct PackedLoad<SpF32, SWAP_DN> {
 // accumulated in AD (order (2, 3)) for mu = 2, 3 and in ADS (order (3, 2)) for mu = 0, 1, so
 // that no pair ever needs its halves exchanged.  The link comes from shared memory as nine
 // float4 (ur, ur, ui, ui), element (a, b) at index 3a + b.
-template <class SP, int MU, bool DAGU>
-__device__ __forceinline__ void hop_dir_packed(const void* in, const float* in_n, size_t hn, int s, int ns,
-                                               bool valid, float sc_sign, float sg, const float4* lnk,
+// Link sources for hop_dir_packed: element (a, b) of U as broadcast pairs (ur, ur), (ui, ui).
+struct LinkStaged {  // nine float4 (ur, ur, ui, ui) in shared memory
+    const float4* q;
+    __device__ __forceinline__ void get(int a, int b, float2& ur, float2& ui) const {
+        const float4 v = q[3 * a + b];
+        ur = make_float2(v.x, v.y);
+        ui = make_float2(v.z, v.w);
+    }
+};
+struct LinkRegs {  // 18 reals held in registers
+    float u[18];
+    __device__ __forceinline__ void get(int a, int b, float2& ur, float2& ui) const {
+        ur = make_float2(u[2 * (3 * a + b)], u[2 * (3 * a + b)]);
+        ui = make_float2(u[2 * (3 * a + b) + 1], u[2 * (3 * a + b) + 1]);
+    }
+};
+
+template <class SP, int MU, bool DAGU, class LF>
+__device__ __forceinline__ void hop_dir_packed(const RawSite<SP>& raw, float sc_sign, float sg, const LF& lnk,
                                                float2 AUr[3], float2 AUi[3], float2 ADr[3], float2 ADi[3],
                                                float2 ADSr[3], float2 ADSi[3]) {
     constexpr bool SW = (MU == 0 || MU == 1);
     float2 Ur[3], Ui[3], Dr[3], Di[3];
-    float sc = 0.f;
-    if (valid) {
-        sc = PackedLoad<SP, SW>::load(in, in_n, hn, s, ns, Ur, Ui, Dr, Di);
-    } else {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) Ur[c] = Ui[c] = Dr[c] = Di[c] = make_float2(0.f, 0.f);
-    }
-    sc *= sc_sign;
+    unpack_site<SP, SW>(raw, Ur, Ui, Dr, Di);
+    const float sc = raw.sc * sc_sign;
     // projection
     float2 Hr[3], Hi[3];
 #pragma unroll
@@ -213,8 +227,8 @@ __device__ __forceinline__ void hop_dir_packed(const void* in, const float* in_n
         Wi[a] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            const float4 q = lnk[DAGU ? 3 * b + a : 3 * a + b];
-            const float2 ur = make_float2(q.x, q.y), ui = make_float2(q.z, q.w);
+            float2 ur, ui;
+            if (DAGU) lnk.get(b, a, ur, ui); else lnk.get(a, b, ur, ui);
             if (!DAGU) {
                 Wr[a] = fma2(ur, Hr[b], fma2(ui, Nh[b], Wr[a]));
                 Wi[a] = fma2(ur, Hi[b], fma2(ui, Hr[b], Wi[a]));
@@ -249,7 +263,7 @@ __device__ __forceinline__ void hop_dir_packed(const void* in, const float* in_n
 constexpr int kLinkStride = 36;                  // floats per staged link: 9 x (ur, ur, ui, ui)
 constexpr int kSiteLinks = 8 * kLinkStride + 4;  // floats per site (padding spreads banks)
 
-template <class SP, class LK, int NS, int KIND>
+template <class SP, class LK, int NS, int KIND, bool GL>
 __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P) {
     constexpr bool DAG = (KIND == K3 || KIND == K4);
     const int sys = blockIdx.y + P.sys_base;
@@ -284,9 +298,9 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
     }
 
     // stage the site's eight links in shared memory: lane d < 8 of the group loads direction d
-    __shared__ __align__(16) float s_links[(kBS2 / NS) * kSiteLinks];
-    float* my_links = s_links + (threadIdx.x / NS) * kSiteLinks;
-    if (s < 8) {
+    __shared__ __align__(16) float s_links[GL ? 4 : (kBS2 / NS) * kSiteLinks];
+    float* my_links = s_links + (GL ? 0 : (threadIdx.x / NS) * kSiteLinks);
+    if (!GL && s < 8) {
         const int mu = s >> 1, dir = s & 1;
         const size_t lidx = dir == 0 ? ((size_t)(p_out * 4 + mu) * P.g.Vh + h)
                                      : ((size_t)(p_in * 4 + mu) * P.g.Vh + nb[s]);
@@ -307,10 +321,28 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
     const float4* L4 = reinterpret_cast<const float4*>(my_links);
     // forward hops use (1 - gamma) for D and (1 + gamma) for D^dag; backward the opposite
     constexpr float SF = DAG ? 1.f : -1.f;
+    // links: staged in shared memory, or (GL) loaded per lane with broadcast global loads
+    // neighbour j + 1 is fetched before neighbour j is processed
+    RawSite<SP> rs[2];
+    fetch_site<SP>(in, in_n, (size_t)nb[0], s, NS, valid, rs[0]);
 #define ODWF_HOP_DIR(MU_, DIR_)                                                                                   \
-    hop_dir_packed<SP, MU_, DIR_ == 1>(in, in_n, (size_t)nb[2 * MU_ + DIR_], s, NS, valid,                        \
-                                       (flip & (1u << (2 * MU_ + DIR_))) ? -1.f : 1.f, DIR_ == 0 ? SF : -SF,     \
-                                       L4 + (2 * MU_ + DIR_) * 9, AUr, AUi, ADr, ADi, ADSr, ADSi)
+    {                                                                                                             \
+        constexpr int j_ = 2 * MU_ + DIR_;                                                                        \
+        if (j_ < 7) fetch_site<SP>(in, in_n, (size_t)nb[j_ + 1 < 8 ? j_ + 1 : 7], s, NS, valid, rs[(j_ + 1) & 1]); \
+        const float sgn_ = (flip & (1u << j_)) ? -1.f : 1.f;                                                     \
+        if (GL) {                                                                                                 \
+            LinkRegs lr_;                                                                                         \
+            const size_t lidx_ = DIR_ == 0 ? ((size_t)(p_out * 4 + MU_) * P.g.Vh + h)                             \
+                                           : ((size_t)(p_in * 4 + MU_) * P.g.Vh + nb[j_]);                        \
+            LinkIO<LK, float>::load(P.links, lidx_, lr_.u);                                                      \
+            hop_dir_packed<SP, MU_, DIR_ == 1>(rs[j_ & 1], sgn_, DIR_ == 0 ? SF : -SF, lr_, AUr, AUi, ADr, ADi,    \
+                                               ADSr, ADSi);                                                       \
+        } else {                                                                                                  \
+            const LinkStaged ls_{L4 + j_ * 9};                                                                    \
+            hop_dir_packed<SP, MU_, DIR_ == 1>(rs[j_ & 1], sgn_, DIR_ == 0 ? SF : -SF, ls_, AUr, AUi, ADr, ADi,    \
+                                               ADSr, ADSi);                                                       \
+        }                                                                                                         \
+    }
     ODWF_HOP_DIR(0, 0); ODWF_HOP_DIR(0, 1);
     ODWF_HOP_DIR(1, 0); ODWF_HOP_DIR(1, 1);
     ODWF_HOP_DIR(2, 0); ODWF_HOP_DIR(2, 1);
@@ -430,16 +462,20 @@ __global__ void __launch_bounds__(kBS2) p_update2_kernel(FieldRef rr, FieldRef p
     if (valid) SpinorIO<SP, float>::store(chi.d(sys), chi.n(sys), h, s, NS, v);
 }
 
+#ifndef ODWF_HOP2_GLOBAL_LINKS
+#define ODWF_HOP2_GLOBAL_LINKS 0
+#endif
 template <class SP, class LK, int NS>
 cudaError_t hop2_k(const HopParams<float>& P, int kind, int nsys, cudaStream_t st) {
+    constexpr bool GL = ODWF_HOP2_GLOBAL_LINKS != 0;
     const size_t n = (size_t)P.g.Vh * NS;
     dim3 grid(blocks_for(n, kBS2), nsys);
     note_launch();
     switch (kind) {
-        case K1: hop2_kernel<SP, LK, NS, K1><<<grid, kBS2, 0, st>>>(P); break;
-        case K2: hop2_kernel<SP, LK, NS, K2><<<grid, kBS2, 0, st>>>(P); break;
-        case K3: hop2_kernel<SP, LK, NS, K3><<<grid, kBS2, 0, st>>>(P); break;
-        default: hop2_kernel<SP, LK, NS, K4><<<grid, kBS2, 0, st>>>(P); break;
+        case K1: hop2_kernel<SP, LK, NS, K1, GL><<<grid, kBS2, 0, st>>>(P); break;
+        case K2: hop2_kernel<SP, LK, NS, K2, GL><<<grid, kBS2, 0, st>>>(P); break;
+        case K3: hop2_kernel<SP, LK, NS, K3, GL><<<grid, kBS2, 0, st>>>(P); break;
+        default: hop2_kernel<SP, LK, NS, K4, GL><<<grid, kBS2, 0, st>>>(P); break;
     }
     return cudaGetLastError();
 }

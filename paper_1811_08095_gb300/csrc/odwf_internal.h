@@ -317,7 +317,11 @@ __device__ __forceinline__ void minv_apply(R v[24], const Coef5<R>& cf, R r, int
 }
 
 // ---------------------------------------------------------------- CG scalar state (device)
-enum SysStatus : int { kRunning = 0, kNeedUpdate = 1, kDone = 2, kBreakdown = 3, kIdle = 4, kMaxIter = 5 };
+// kRestarting: a reliable update has recomputed the residual and restarted the inner
+// iteration on the update stream; the iteration stream switches it back to kRunning once
+// it has waited for that work (state_kernel mode 2).
+enum SysStatus : int { kRunning = 0, kNeedUpdate = 1, kDone = 2, kBreakdown = 3, kIdle = 4, kMaxIter = 5,
+                       kRestarting = 6 };
 
 struct SysState {
     double rr;       // inner ||r||^2 of the current iterate

@@ -100,7 +100,8 @@ constexpr int kIterChunk = 8;
 size_t per_system_bytes(size_t sites5, int prec) {
     if (prec == ODWF_F64) return sites5 * 192 * 7;
     const size_t lowb = prec == ODWF_F32 ? 96 : 52;
-    return sites5 * (192 * 3 + 96 * 2 + lowb * 4);
+    // FP64 x, a device copy of a host b, FP32 r and x, five low-precision fields
+    return sites5 * (192 * 2 + 96 * 2 + lowb * 5);
 }
 
 size_t group_fixed_bytes(size_t vh, size_t sites5) {
@@ -186,19 +187,8 @@ bool try_admit(serve_handle* S, const std::shared_ptr<Request>& R, std::unique_l
     std::vector<int> slots;
     for (int i = 0; i < (int)G->slot_req.size() && (int)slots.size() < q.nrhs; ++i)
         if (!G->slot_req[i]) slots.push_back(i);
-    const size_t eb = sites5 * 192;
     for (int k = 0; k < q.nrhs && !rc; ++k) {
-        const void* b = R->b[k];
-        const double2* db = (const double2*)b;
-        if (!is_device_ptr(b)) {
-            void* d = G->eng->get_ws("serve.b", eb, &rc);
-            if (rc) break;
-            if (cudaMemcpyAsync(d, b, eb, cudaMemcpyHostToDevice, G->stream) != cudaSuccess) {
-                rc = ODWF_ECUDA;
-                break;
-            }
-            db = (const double2*)d;
-        }
+        const double2* db = (const double2*)R->b[k];  // host data is copied per slot by admit()
         rc = G->cg->admit(slots[k], db, q.mq, G->stream, q.tol, q.max_iter);
     }
     lk.lock();
@@ -262,7 +252,10 @@ void worker_loop(serve_handle* S) {
         for (auto& g : S->groups)
             if (g->cg && g->cg->any_running()) act.push_back(g.get());
         lk.unlock();
-        for (Group* g : act) g->cg->run_iterations(kIterChunk, g->stream);
+        for (Group* g : act) {
+            g->cg->resume(g->stream, false);
+            g->cg->run_iterations(kIterChunk, g->stream);
+        }
         // 3. poll, reliable updates, completions
         for (Group* g : act) {
             BatchCG& cg = *g->cg;
