@@ -132,14 +132,15 @@ def measured_peaks():
 
 
 def ncu_traffic(kernel_class):
-    """dram bytes per launch for a kernel class from the committed ncu summary, if present."""
+    """(dram bytes per launch, running systems in that launch) for a kernel class from the
+    committed ncu summary, if present."""
     if not os.path.exists(NCU_TRAFFIC):
         return None
     for line in open(NCU_TRAFFIC):
         parts = line.split()
-        if len(parts) >= 2 and not line.startswith("#") and parts[0] == kernel_class:
+        if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel_class:
             try:
-                return float(parts[1])
+                return float(parts[1]), int(parts[2])
             except ValueError:
                 return None
     return None
@@ -261,7 +262,13 @@ def run_ours(args, world, rank, local):
             / dom["launches"]
         avg_s = dom["total_ms"] / dom["launches"] / 1e3
         achieved = per_launch / avg_s / 1e9
-        tr = ncu_traffic(dom["name"])
+        # ncu traffic of a captured launch, scaled to this run's average launch by algorithmic bytes
+        tr = None
+        cap = ncu_traffic(dom["name"])
+        if cap:
+            cap_bytes, cap_sys = cap
+            cap_alg = cap_sys * dom["bytes_per_system"] + dom["bytes_per_launch"]
+            tr = round(cap_bytes * per_launch / cap_alg)
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": tr, "kernel": dom["name"],
                 "algorithmic_bytes_per_launch": per_launch, "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)"}
@@ -361,14 +368,10 @@ def run_serve(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     rng = np.random.default_rng(21)
-    srv = odwf.Server(0)
-    vols = []
-    for k, dims in enumerate(SERVE_LATTICES):
-        U = syn.gauge_field_torch(dims, EPS, 11 + k, device=dev)
-        srv.register_gauge(k, dims, U)
-        vols.append(dims[0] * dims[1] * dims[2] * dims[3])
-        del U
+    vols = [d[0] * d[1] * d[2] * d[3] for d in SERVE_LATTICES]
     omegas = {ns: odwf.odwf_zolotarev_omega(ns, LRANGE[0], LRANGE[1])[0] for ns in (8, 16)}
+    # the client's buffers first, so that the server's budget (90% of the free memory at
+    # serve_create) counts only what is left for it
     pool = {}
     g = torch.Generator(device=dev)
     g.manual_seed(1234)
@@ -378,6 +381,14 @@ def run_serve(args, world, rank, local):
             bs = [torch.randn(shape, dtype=torch.complex128, device=dev, generator=g) for _ in range(12)]
             xs = [torch.zeros(shape, dtype=torch.complex128, device=dev) for _ in range(12)]
             pool[(k, ns)] = (bs, xs)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    srv = odwf.Server(0)
+    for k, dims in enumerate(SERVE_LATTICES):
+        U = syn.gauge_field_torch(dims, EPS, 11 + k, device=dev)
+        srv.register_gauge(k, dims, U)
+        del U
+        torch.cuda.empty_cache()
     torch.cuda.synchronize()
     rate, duration, drain = args.rate, args.duration, args.drain
     t0 = time.perf_counter()
@@ -408,9 +419,22 @@ def run_serve(args, world, rank, local):
     wall = time.perf_counter() - t0
     lat = np.array([d[0] for d in done]) if done else np.array([float("nan")])
     bad = [d for d in done if d[2] != 0]
+    codes = {}
+    for d in bad:
+        codes[str(d[2])] = codes.get(str(d[2]), 0) + 1
+    per_lat = {}
+    for d in done:
+        key = "x".join(str(v) for v in SERVE_LATTICES[d[4]]) + "/Ns%d" % d[5]
+        e = per_lat.setdefault(key, {"completed": 0, "p50_ms": [], "solves": 0})
+        e["completed"] += 1
+        e["solves"] += d[3]
+        e["p50_ms"].append(d[0])
+    for e in per_lat.values():
+        e["p50_ms"] = round(float(np.percentile(e["p50_ms"], 50)), 1)
     line = {"metric": "served ODWF D\u2020D solve latency (p50/p99) and throughput", "workload": "serve_poisson",
             "rate_req_s": rate, "duration_s": duration, "submitted": submitted, "completed": len(done),
-            "pending_at_end": len(pending), "failed": len(bad), "wall_s": round(wall, 2),
+            "pending_at_end": len(pending), "failed": len(bad), "failed_codes": codes, "per_lattice": per_lat,
+            "wall_s": round(wall, 2),
             "p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2),
             "throughput_req_s": round(len(done) / wall, 3), "throughput_solves_s": round(solves_done / wall, 3),
             "max_true_resid": max([d[6] for d in done], default=None),

@@ -196,13 +196,13 @@ int BatchCG::admit_internal(int slot, cudaStream_t s, double tol_slot, int max_i
         ODWF_CK(launch_vec(Sp::F64, Sp::F64, B, R64.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
         ODWF_CK(launch_vec(Sp::F64, Sp::F64, B, P64.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
     } else {
-        ODWF_CK(launch_vec(Sp::F64, Sp::F32, B, Rin.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
+        ODWF_CK(launch_vec(Sp::F64, Sp::F32, B, Rin.ref(), n5, ns, 6, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
         ODWF_CK(launch_vec(Sp::F32, Sp::F32, Xin.ref(), Xin.ref(), n5, ns, 5, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
         if (v2) {
             ODWF_CK(launch_p_update2(low, ns, Rin.ref(), Pl.ref(), Chil.ref(), E->vh(), 0, E->cf32, r_dev, st, 0, 0,
                                      slot, 1, nullptr, s));
         } else {
-            ODWF_CK(launch_vec(Sp::F64, low, B, Pl.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
+            ODWF_CK(launch_vec(Sp::F64, low, B, Pl.ref(), n5, ns, 6, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
         }
     }
     active[slot] = 1;
@@ -421,15 +421,15 @@ int BatchCG::service(cudaStream_t s) {
         ODWF_CK(cudaEventRecord(ev_rel[i], s));
         ODWF_CK(cudaStreamWaitEvent(s_rel, ev_rel[i], 0));
         cudaStream_t r = s_rel;
-        if (mixed)  // X64 += x_in, x_in = 0
-            ODWF_CK(launch_vec(Sp::F32, Sp::F64, Xin.ref(), X64.ref(), n5, E->ns, 2, 0.0, st, 0, 0, nullptr, nullptr,
+        if (mixed)  // X64 += rscale x_in, x_in = 0
+            ODWF_CK(launch_vec(Sp::F32, Sp::F64, Xin.ref(), X64.ref(), n5, E->ns, 7, 0.0, st, 0, 0, nullptr, nullptr,
                                i, 1, r));
         int rc = load_b(i, r);
         if (!rc) rc = fp64_residual(i, r);
         if (rc) return rc;
         ODWF_CK(launch_state(st + i, 1, 1, tol * tol, r));  // done / max-iter / kRestarting
         if (mixed) {
-            ODWF_CK(launch_vec(Sp::F64, Sp::F32, Rref(), Rin.ref(), n5, E->ns, 0, 0.0, st, 1, kRestarting, nullptr,
+            ODWF_CK(launch_vec(Sp::F64, Sp::F32, Rref(), Rin.ref(), n5, E->ns, 6, 0.0, st, 1, kRestarting, nullptr,
                                nullptr, i, 1, r));
             if (v2) {
                 ODWF_CK(launch_p_update2(low, E->ns, Rin.ref(), Pl.ref(), Chil.ref(), E->vh(), 1, E->cf32, r_dev, st,
@@ -462,7 +462,7 @@ int BatchCG::finalize(int slot, double2* x_ext, cudaStream_t s, double* true_res
         // breakdown (or an unfinished slot): fold and recompute the true residual
         int rc = ODWF_OK;
         if (mixed) {
-            ODWF_CK(launch_vec(Sp::F32, Sp::F64, Xin.ref(), X64.ref(), E->sites5(), E->ns, 2, 0.0, st, 0, 0, nullptr,
+            ODWF_CK(launch_vec(Sp::F32, Sp::F64, Xin.ref(), X64.ref(), E->sites5(), E->ns, 7, 0.0, st, 0, 0, nullptr,
                                nullptr, slot, 1, s));
             rc = order_after(s_rel, s);  // the shared FP64 buffers are free
             if (!rc) rc = load_b(slot, s);

@@ -195,13 +195,22 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     return v;
 }
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    return v;
+}
 
 // Deterministic block sum (fixed tree for a fixed blockDim); result valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double* sm) {
+// The per-thread values and the sum over a warp are taken in the kernel's arithmetic type
+// R (FP32 in the mixed-precision kernels: GB300's FP64 rate is a small fraction of its
+// FP32 rate), the sums across warps, blocks and the grid in FP64.
+template <class R>
+__device__ __forceinline__ double block_sum(R v, double* sm) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     v = warp_sum(v);
     __syncthreads();
-    if (lane == 0) sm[wid] = v;
+    if (lane == 0) sm[wid] = (double)v;
     __syncthreads();
     double t = 0.0;
     if (wid == 0) {
@@ -227,7 +236,7 @@ __device__ __forceinline__ void finalize_scalar(SysState* st, double total, int 
         st->iter += 1;
         if (!isfinite(rr_new)) {
             st->status = kBreakdown;
-        } else if (rr_new <= st->stop_rr || st->iter >= st->max_iter ||
+        } else if (rr_new <= st->stop_in || st->iter >= st->max_iter ||
                    (st->reliable && sqrt(rr_new) < st->delta * st->r_max)) {
             // park the system: the host recomputes the true residual in FP64 (and, in mixed
             // precision, folds the inner solution into the FP64 one) before it continues
@@ -242,7 +251,8 @@ __device__ __forceinline__ void finalize_scalar(SysState* st, double total, int 
 
 // Block-level reduction of `v` for system `sys`; the last block to arrive sums the
 // partials in index order and finalizes.
-__device__ __forceinline__ void reduce_and_finalize(double v, double* partials, unsigned* counters, SysState* st,
+template <class R>
+__device__ __forceinline__ void reduce_and_finalize(R v, double* partials, unsigned* counters, SysState* st,
                                                     int sys, int fin) {
     __shared__ double sm[32];
     __shared__ bool is_last;
@@ -260,7 +270,7 @@ __device__ __forceinline__ void reduce_and_finalize(double v, double* partials, 
     __threadfence();
     double t = 0.0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) t += *((volatile double*)(part + i));
-    const double total = block_sum(t, sm);
+    const double total = block_sum<double>(t, sm);
     if (threadIdx.x == 0) {
         finalize_scalar(st + sys, total, fin);
         counters[sys] = 0u;
@@ -366,10 +376,10 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams<R> P) {
         for (int k = 0; k < 24; ++k) res[k] = NEG ? -acc[k] : acc[k];
     }
 
-    double nrm = 0.0;
+    R nrm = R(0);  // per-thread partial sum in the arithmetic type (see block_sum)
     if (NORM && valid) {
 #pragma unroll
-        for (int k = 0; k < 24; ++k) nrm += (double)res[k] * (double)res[k];
+        for (int k = 0; k < 24; ++k) nrm += res[k] * res[k];
     }
     if (POST == OP_MINV) minv_apply(res, P.cf, r, s, ns, false);
     if (POST == OP_MINVDAG) minv_apply(res, P.cf, r, s, ns, true);
@@ -386,7 +396,7 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams<R> P) {
             for (int k = 0; k < 24; ++k) {
                 rv[k] -= alpha * res[k];
                 xv[k] += alpha * pv[k];
-                nrm += (double)rv[k] * (double)rv[k];
+                nrm += rv[k] * rv[k];
             }
             SpinorIO<SPacc, R>::store(P.cg_r.d(sys), P.cg_r.n(sys), (size_t)h, s, ns, rv);
             SpinorIO<SPacc, R>::store(P.cg_x.d(sys), P.cg_x.n(sys), (size_t)h, s, ns, xv);
@@ -398,7 +408,7 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams<R> P) {
 #pragma unroll
             for (int k = 0; k < 24; ++k) {
                 res[k] = bv[k] - res[k];
-                nrm += (double)res[k] * (double)res[k];
+                nrm += res[k] * res[k];
             }
             SpinorIO<SPout, R>::store(P.out.d(sys), P.out.n(sys), (size_t)h, s, ns, res);
         }
@@ -496,6 +506,8 @@ __global__ void __launch_bounds__(256) unpack_kernel(FieldRef in, double2* __res
 //   kind 3: |x|^2 -> reduction (FIN_STORE into state.sum)
 //   kind 4: y = a x + y  (a = coef)
 //   kind 5: y = 0
+//   kind 6: y = x / rscale                  (true residual -> inner units)
+//   kind 7: X += rscale x ; x = 0           (fold the inner solution, inner -> true units)
 template <class SPx, class SPy, class R>
 __global__ void __launch_bounds__(256) vec_kernel(FieldRef x, FieldRef y, size_t n5, int ns, int kind, double coef,
                                                   SysState* st, int gate, int need, double* partials,
@@ -536,6 +548,22 @@ __global__ void __launch_bounds__(256) vec_kernel(FieldRef x, FieldRef y, size_t
 #pragma unroll
                 for (int k = 0; k < 24; ++k) nrm += (double)a[k] * (double)a[k];
                 break;
+            case 6: {
+                const R inv = (R)(1.0 / st[sys].rscale);
+#pragma unroll
+                for (int k = 0; k < 24; ++k) a[k] *= inv;
+                SpinorIO<SPy, R>::store(y.d(sys), y.n(sys), h, s, ns, a);
+                break;
+            }
+            case 7: {
+                const R sc = (R)st[sys].rscale;
+                SpinorIO<SPy, R>::load(y.d(sys), y.n(sys), h, s, ns, b);
+#pragma unroll
+                for (int k = 0; k < 24; ++k) { b[k] += sc * a[k]; a[k] = 0; }
+                SpinorIO<SPy, R>::store(y.d(sys), y.n(sys), h, s, ns, b);
+                SpinorIO<SPx, R>::store(x.d(sys), x.n(sys), h, s, ns, a);
+                break;
+            }
             case 4: {
                 SpinorIO<SPy, R>::load(y.d(sys), y.n(sys), h, s, ns, b);
 #pragma unroll
@@ -551,7 +579,7 @@ __global__ void __launch_bounds__(256) vec_kernel(FieldRef x, FieldRef y, size_t
             }
         }
     }
-    if (kind == 3) reduce_and_finalize(nrm, partials, counters, st, sys, FIN_STORE);
+    if (kind == 3) reduce_and_finalize<double>(nrm, partials, counters, st, sys, FIN_STORE);
 }
 
 }  // namespace odwf

@@ -138,9 +138,10 @@ cudaError_t launch_vec(Sp spx, Sp spy, const FieldRef& x, const FieldRef& y, siz
 }
 
 // One thread per system: CG bookkeeping between phases.
-//   mode 0 (init):  rr = bb = sum, r_max = sqrt(sum), status running (done when b = 0)
+//   mode 0 (init):  bb = sum; mixed precision: rscale = |b|, rr = r_max = 1; plain CG:
+//                   rr = sum, r_max = |b|; status running (done when b = 0)
 //   mode 1 (after a reliable update, sum = ||b - A x||^2): done / max-iter / restart with
-//                   beta = sum / rr_prev, rr = sum, r_max = sqrt(sum) (status kRestarting)
+//                   the continued beta, rscale = |r| (mixed), rr, r_max (status kRestarting)
 //   mode 2:         kRestarting -> kRunning (launched on the iteration stream)
 __global__ void state_kernel(SysState* st, int nsys, int mode, double tol2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -148,9 +149,18 @@ __global__ void state_kernel(SysState* st, int nsys, int mode, double tol2) {
     SysState& S = st[i];
     if (mode == 0) {
         S.bb = S.sum;
-        S.rr = S.sum;
         S.stop_rr = tol2 * S.sum;
-        S.r_max = sqrt(S.sum);
+        if (S.reliable && S.sum > 0.0) {
+            S.rscale = sqrt(S.sum);
+            S.rr = 1.0;
+            S.r_max = 1.0;
+            S.stop_in = tol2;
+        } else {
+            S.rscale = 1.0;
+            S.rr = S.sum;
+            S.r_max = sqrt(S.sum);
+            S.stop_in = S.stop_rr;
+        }
         S.iter = 0;
         S.alpha = S.beta = 0.0;
         S.status = (S.sum > 0.0) ? kRunning : kDone;
@@ -158,19 +168,23 @@ __global__ void state_kernel(SysState* st, int nsys, int mode, double tol2) {
         if (S.status == kRestarting) S.status = kRunning;
     } else {
         if (S.status != kNeedUpdate) return;
-        const double rt = S.sum;
+        const double rt = S.sum;  // true |r|^2 of the recomputed residual
         if (!isfinite(rt)) {
             S.status = kBreakdown;
         } else if (rt <= S.stop_rr) {
-            S.rr = rt;
             S.status = kDone;
         } else if (S.iter >= S.max_iter) {
-            S.rr = rt;
             S.status = kMaxIter;
         } else {
-            S.beta = rt / S.rr;
-            S.rr = rt;
-            S.r_max = sqrt(rt);
+            // continue the search direction: p_true = r_true + beta_true p_true, written in
+            // the new inner units (p_inner = p_true / rscale)
+            const double s_old = S.rscale;
+            const double s_new = S.reliable ? sqrt(rt) : 1.0;
+            S.beta = rt / (S.rr * s_old * s_old) * (s_old / s_new);
+            S.rscale = s_new;
+            S.rr = rt / (s_new * s_new);
+            S.r_max = sqrt(S.rr);
+            S.stop_in = S.stop_rr / (s_new * s_new);
             S.status = kRestarting;
         }
     }

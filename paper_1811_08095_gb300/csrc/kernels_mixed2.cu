@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
     }
 
     const Coef5<float>& cf = P.cf;
-    double nrm = 0.0;
+    float nrm = 0.f;  // per-thread partial sums in FP32, FP64 across warps and blocks (block_sum)
     if (KIND == K1) {
         // chi_t = B M^-1 (-1/2 y)
 #pragma unroll
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
 #pragma unroll
         for (int k = 0; k < 24; ++k) {
             acc[k] += z[k];
-            nrm += (double)acc[k] * (double)acc[k];
+            nrm = fmaf(acc[k], acc[k], nrm);
         }
         minv_apply(acc, cf, r, s, NS, true);
         if (valid) SpinorIO<SP, float>::store(P.out.d(sys), P.out.n(sys), (size_t)h, s, NS, acc);
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
                 const float ap = fmaf(0.5f, acc[k], z[k]);
                 rv[k] = fmaf(-alpha, ap, rv[k]);
                 xv[k] = fmaf(alpha, pv[k], xv[k]);
-                nrm += (double)rv[k] * (double)rv[k];
+                nrm = fmaf(rv[k], rv[k], nrm);
             }
             SpinorIO<SpF32, float>::store(P.cg_r.d(sys), nullptr, (size_t)h, s, NS, rv);
             SpinorIO<SpF32, float>::store(P.cg_x.d(sys), nullptr, (size_t)h, s, NS, xv);

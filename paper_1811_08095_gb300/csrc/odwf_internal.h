@@ -333,6 +333,13 @@ struct SysState {
     double stop_rr;  // tol^2 ||b||^2
     double delta;    // reliable-update threshold
     double sum;      // generic reduction result
+    // Mixed precision solves the inner system for r / rscale, rscale = |r| at the last
+    // (re)start, so the inner fields stay near unit norm (FP16/BF16 range, and no FP32
+    // underflow of squared components late in a solve); plain CG keeps rscale = 1.
+    // rr, r_max and stop_in are in inner units, bb, stop_rr and sum in true units.
+    double rscale;
+    double stop_in;  // inner stopping threshold on rr
+
     int status;
     int iter;
     int max_iter;
