@@ -60,7 +60,7 @@ int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStr
             (rc = E->alloc_half("cg.A1", Sp::F64, 1, &A1)) || (rc = E->alloc_half("cg.C1", Sp::F64, 1, &C1)))
             return rc;
         if ((rc = E->ensure_links(lk, s))) return rc;
-        v2 = hop2_supported(E->ns, low);
+        v2 = hop2_supported(E->ns, low, E->vh());
         if (v2 && (rc = E->alloc_half(tag + ".X", low, cap, &Chil))) return rc;
     }
     st = (SysState*)E->get_ws("cg.state", sizeof(SysState) * cap, &rc);
@@ -85,7 +85,9 @@ int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStr
     ODWF_CK(cudaStreamSynchronize(s));
     n_reliable.assign(cap, 0);
     upd.assign(cap, 0);
-    ODWF_CK(cudaStreamCreateWithFlags(&s_rel, cudaStreamNonBlocking));
+    int prio = 0;  // the update stream takes the iteration stream's priority
+    if (s) ODWF_CK(cudaStreamGetPriority(s, &prio));
+    ODWF_CK(cudaStreamCreateWithPriority(&s_rel, cudaStreamNonBlocking, prio));
     ODWF_CK(cudaEventCreateWithFlags(&ev_sync, cudaEventDisableTiming));
     bsrc.assign(cap, nullptr);
     ev_rel.assign(cap, nullptr);
@@ -389,16 +391,23 @@ int BatchCG::fp64_residual(int slot, cudaStream_t s) {
         a = A64.ref();
         c = C64.ref();
     }
+    // The non-dagger hops read chi = B psi, shifted once per site beforehand into c (free
+    // until the third hop writes it) instead of once per neighbour inside the hop.
+    const size_t vh = E->vh();
+    ODWF_CK(launch_m5_f64(X.ref(), c, vh, E->ns, r_dev, slot, 1, 4, E->cf64, s));
     auto P = params<double>(1);
     P.sys_base = slot;
-    P.in = X.ref();
+    P.preshifted = 1;
+    P.in = c;
     P.out = t;
     { auto pb_ = prof_begin(pcls_rel[0], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_f64(P, Epi::MINV, 1, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+    ODWF_CK(launch_m5_f64(t, c, vh, E->ns, r_dev, slot, 1, 4, E->cf64, s));
     P.p_out = 0;
-    P.in = t;
+    P.in = c;
     P.z = X.ref();
     P.out = a;
     { auto pb_ = prof_begin(pcls_rel[1], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_f64(P, Epi::SCHUR_MDINV, 1, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+    P.preshifted = 0;
     P.p_out = 1;
     P.in = a;
     P.z = FieldRef{};

@@ -37,6 +37,7 @@ Engine::~Engine() {
     if (links_d18) cudaFree(links_d18);
     if (links_f18) cudaFree(links_f18);
     if (links_f12) cudaFree(links_f12);
+    if (nbr) cudaFree(nbr);
     if (pinned) cudaFreeHost(pinned);
 }
 
@@ -179,6 +180,10 @@ int Engine::set_gauge(const void* U, cudaStream_t st) {
 int Engine::ensure_links(Lk lk, cudaStream_t st) {
     if (!gauge_set) return fail(ODWF_EINVAL, "gauge field not set");
     const size_t nl = 8 * vh();
+    if (!nbr) {
+        ODWF_CK(cudaMalloc(&nbr, 2 * nl * sizeof(int)));
+        ODWF_CK(launch_build_neighbours(nbr, g, st));
+    }
     if (lk == Lk::F12 && !have_f12) {
         if (!links_f12) ODWF_CK(cudaMalloc(&links_f12, nl * 48));
         ODWF_CK(launch_links_from_d18(links_d18, nullptr, links_f12, nl, st));
@@ -214,6 +219,7 @@ HopParams<float> Engine::hop_params<float>(int p_out, const double* r_dev) const
     P.lg_ns = lg_ns;
     P.p_out = p_out;
     P.links = links_f12;
+    P.nbr = nbr;
     P.r_sys = r_dev;
     P.cf = cf32;
     return P;

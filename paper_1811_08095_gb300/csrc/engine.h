@@ -60,6 +60,7 @@ struct Engine {
     void* links_d18 = nullptr;
     void* links_f18 = nullptr;
     void* links_f12 = nullptr;
+    int* nbr = nullptr;  // neighbour table of the second-generation hops (launch_build_neighbours)
     bool gauge_set = false;
     bool have_f12 = false, have_f18 = false;  // FP32 link copies derived from the FP64 ones
 

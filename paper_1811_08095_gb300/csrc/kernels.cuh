@@ -78,10 +78,12 @@ struct HopParams {
     int ns;
     int lg_ns;
     int p_out;           // parity of the output sites
+    int preshifted;      // non-dagger hops: `in` already holds chi = B psi (skip B per neighbour)
     FieldRef in, z, out;
     FieldRef cg_r, cg_x, cg_p;  // F_CG: r and x (accumulator format), p (input format)
     FieldRef b;                 // F_RESID: right-hand side (accumulator format)
     const void* links;
+    const int* nbr;             // neighbour table (second-generation hops), see launch_build_neighbours
     const double* r_sys;        // per-system r = m_q / (2 m0)
     int gate;                   // 1: run only systems whose st[sys].status == need_status
     int need_status;
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams<R> P) {
 #pragma unroll
                 for (int k = 0; k < 24; ++k) v[k] = 0;
             }
-            if (!DAG) bidiag_apply(v, P.cf.rho[s], P.cf.sigma[s], r, s, ns, false);  // chi = B psi
+            if (!DAG && !P.preshifted) bidiag_apply(v, P.cf.rho[s], P.cf.sigma[s], r, s, ns, false);  // chi = B psi
 
             // forward hop uses (1 - gamma) for D and (1 + gamma) for D^dag; backward the opposite
             const R sg = DAG ? (dir == 0 ? (R)1 : (R)-1) : (dir == 0 ? (R)-1 : (R)1);
@@ -440,7 +442,8 @@ __global__ void __launch_bounds__(256) m5_kernel(FieldRef in, FieldRef out, size
     if (op == 0) bidiag_apply(v, cf.d[s], cf.e[s], r, s, ns, false);
     else if (op == 1) bidiag_apply(v, cf.d[s], cf.e[s], r, s, ns, true);
     else if (op == 2) minv_apply(v, cf, r, s, ns, false);
-    else minv_apply(v, cf, r, s, ns, true);
+    else if (op == 3) minv_apply(v, cf, r, s, ns, true);
+    else bidiag_apply(v, cf.rho[s], cf.sigma[s], r, s, ns, false);  // op 4: chi = B psi (internal)
     if (valid) SpinorIO<SPout, R>::store(out.d(sys), out.n(sys), h, s, ns, v);
 }
 

@@ -42,7 +42,7 @@ cudaError_t launch_hop_mixed(const HopParams<float>& P, Epi e, Sp low, Lk lk, in
 
 // Second-generation mixed CG kernels (Ns = 8 or 16): kind 1..4 = K1..K4 of the iteration
 // (see kernels_mixed2.cu); the non-dagger hops read chi = B psi fields.
-bool hop2_supported(int ns, Sp low);
+bool hop2_supported(int ns, Sp low, size_t vh);
 cudaError_t launch_hop2(const HopParams<float>& P, int kind, Sp low, Lk lk, int nsys, cudaStream_t st);
 // p = r (mode 0) or p = r + beta p (mode 1), and chi = B p
 cudaError_t launch_p_update2(Sp low, int ns, const FieldRef& r, const FieldRef& p, const FieldRef& chi,
@@ -50,7 +50,7 @@ cudaError_t launch_p_update2(Sp low, int ns, const FieldRef& r, const FieldRef& 
                              int gate, int need, int sys_base, int nsys, unsigned long long* prof,
                              cudaStream_t stream);
 
-// Site-local M, M^dag, M^-1, M^-dag (op 0..3)
+// Site-local M, M^dag, M^-1, M^-dag (op 0..3); op 4 = B (the chiral shift rho + sigma L)
 cudaError_t launch_m5_f64(const FieldRef& in, const FieldRef& out, size_t n_sites, int ns, const double* r_sys,
                           int sys_base, int nsys, int op, const Coef5<double>& cf, cudaStream_t st);
 cudaError_t launch_m5_mixed(Sp low, const FieldRef& in, const FieldRef& out, size_t n_sites, int ns,
@@ -78,6 +78,10 @@ cudaError_t launch_pack_links(const double2* U, void* d18, void* f18, void* f12,
 
 // FP32 links (18 reals padded to 20, or the first two rows) from the packed FP64 links
 cudaError_t launch_links_from_d18(const void* d18, void* f18, void* f12, size_t n_links, cudaStream_t st);
+// Neighbour table: for each parity p and half site h, the half indices of the eight
+// neighbours (x+, x-, y+, y-, z+, z-, t+, t-) in the other parity, bit 31 set where the hop
+// crosses the antiperiodic time boundary.  nbr[(p * Vh + h) * 8 + j], 2 * Vh * 8 ints.
+cudaError_t launch_build_neighbours(int* nbr, const Geom& g, cudaStream_t st);
 
 int lg2(int v);
 

@@ -232,6 +232,31 @@ __global__ void links_from_d18_kernel(const double* __restrict__ d18, float* f18
         for (int k = 0; k < 12; ++k) f12[i * 12 + k] = (float)src[k];
 }
 
+__global__ void build_neighbours_kernel(int* nbr, Geom g) {
+    const size_t gi = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= 2 * (size_t)g.Vh) return;
+    const int p = (int)(gi / g.Vh), h = (int)(gi % g.Vh);
+    int c[4];
+    site_coords(g, p, h, c);
+    int* out = nbr + gi * 8;
+    for (int mu = 0; mu < 4; ++mu) {
+        const int Lm = g.L[mu];
+        int cf[4] = {c[0], c[1], c[2], c[3]}, cb[4] = {c[0], c[1], c[2], c[3]};
+        cf[mu] = c[mu] + 1 == Lm ? 0 : c[mu] + 1;
+        cb[mu] = c[mu] == 0 ? Lm - 1 : c[mu] - 1;
+        const bool flip_f = mu == 3 && g.tbc && c[3] == Lm - 1;
+        const bool flip_b = mu == 3 && g.tbc && c[3] == 0;
+        out[2 * mu] = (int)((unsigned)half_index(g, cf) | (flip_f ? 0x80000000u : 0u));
+        out[2 * mu + 1] = (int)((unsigned)half_index(g, cb) | (flip_b ? 0x80000000u : 0u));
+    }
+}
+
+cudaError_t launch_build_neighbours(int* nbr, const Geom& g, cudaStream_t st) {
+    note_launch();
+    build_neighbours_kernel<<<blocks_for(2 * (size_t)g.Vh, 256), 256, 0, st>>>(nbr, g);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_links_from_d18(const void* d18, void* f18, void* f12, size_t n_links, cudaStream_t st) {
     note_launch();
     links_from_d18_kernel<<<blocks_for(n_links, 256), 256, 0, st>>>((const double*)d18, (float*)f18, (float*)f12,

@@ -117,21 +117,22 @@ struct RawSite<SpBF16> { uint4 q[3]; float sc; };
 template <>
 struct RawSite<SpF32> { float4 q[6]; float sc; };
 
+// 32-bit chunk index of (h, s): h * nch * ns + s (hop2_supported bounds the field size)
 template <class SP>
-__device__ __forceinline__ void fetch_site(const void* base, const float* norm, size_t h, int s, int ns, bool valid,
+__device__ __forceinline__ void fetch_site(const void* base, const float* norm, unsigned h, int s, int ns, bool valid,
                                            RawSite<SP>& r) {
     if (std::is_same<SP, SpF32>::value) {
-        const float4* p = reinterpret_cast<const float4*>(base);
+        const float4* p = reinterpret_cast<const float4*>(base) + (h * (6u * ns) + (unsigned)s);
         float4* q = reinterpret_cast<float4*>(&r);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) q[k] = valid ? __ldg(p + chunk_off(h, k, 6, ns, s)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < 6; ++k) q[k] = valid ? __ldg(p + k * ns) : make_float4(0.f, 0.f, 0.f, 0.f);
         r.sc = 1.f;
     } else {
-        const uint4* p = reinterpret_cast<const uint4*>(base);
+        const uint4* p = reinterpret_cast<const uint4*>(base) + (h * (3u * ns) + (unsigned)s);
         uint4* q = reinterpret_cast<uint4*>(&r);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) q[k] = valid ? __ldg(p + chunk_off(h, k, 3, ns, s)) : make_uint4(0u, 0u, 0u, 0u);
-        r.sc = valid ? __ldg(norm + h * ns + s) : 0.f;
+        for (int k = 0; k < 3; ++k) q[k] = valid ? __ldg(p + k * ns) : make_uint4(0u, 0u, 0u, 0u);
+        r.sc = valid ? __ldg(norm + (h * (unsigned)ns + (unsigned)s)) : 0.f;
     }
 }
 
@@ -278,23 +279,18 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
     const float r = (float)P.r_sys[sys];
     const int p_out = P.p_out, p_in = 1 - p_out;
 
-    // the eight neighbours of this site: half index and time-boundary sign
-    int c[4];
-    site_coords(P.g, p_out, h, c);
+    // the eight neighbours of this site (half index) and their time-boundary signs (bit j)
     int nb[8];
     unsigned flip = 0;
+    {
+        const int4* tp = reinterpret_cast<const int4*>(P.nbr + ((size_t)p_out * P.g.Vh + h) * 8);
+        const int4 n0 = __ldg(tp), n1 = __ldg(tp + 1);
+        const int raw[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
 #pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-        const int Lm = P.g.L[mu];
-        int cf[4] = {c[0], c[1], c[2], c[3]}, cb[4] = {c[0], c[1], c[2], c[3]};
-        cf[mu] = c[mu] + 1 == Lm ? 0 : c[mu] + 1;
-        cb[mu] = c[mu] == 0 ? Lm - 1 : c[mu] - 1;
-        nb[2 * mu] = half_index(P.g, cf);
-        nb[2 * mu + 1] = half_index(P.g, cb);
-    }
-    if (P.g.tbc) {
-        if (c[3] == P.g.L[3] - 1) flip |= 1u << 6;
-        if (c[3] == 0) flip |= 1u << 7;
+        for (int j = 0; j < 8; ++j) {
+            nb[j] = raw[j] & 0x7fffffff;
+            flip |= ((unsigned)raw[j] >> 31) << j;
+        }
     }
 
     // stage the site's eight links in shared memory: lane d < 8 of the group loads direction d
@@ -324,11 +320,11 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
     // links: staged in shared memory, or (GL) loaded per lane with broadcast global loads
     // neighbour j + 1 is fetched before neighbour j is processed
     RawSite<SP> rs[2];
-    fetch_site<SP>(in, in_n, (size_t)nb[0], s, NS, valid, rs[0]);
+    fetch_site<SP>(in, in_n, (unsigned)nb[0], s, NS, valid, rs[0]);
 #define ODWF_HOP_DIR(MU_, DIR_)                                                                                   \
     {                                                                                                             \
         constexpr int j_ = 2 * MU_ + DIR_;                                                                        \
-        if (j_ < 7) fetch_site<SP>(in, in_n, (size_t)nb[j_ + 1 < 8 ? j_ + 1 : 7], s, NS, valid, rs[(j_ + 1) & 1]); \
+        if (j_ < 7) fetch_site<SP>(in, in_n, (unsigned)nb[j_ + 1 < 8 ? j_ + 1 : 7], s, NS, valid, rs[(j_ + 1) & 1]); \
         const float sgn_ = (flip & (1u << j_)) ? -1.f : 1.f;                                                     \
         if (GL) {                                                                                                 \
             LinkRegs lr_;                                                                                         \
@@ -518,7 +514,11 @@ cudaError_t pupd_ns(int ns, const FieldRef& r, const FieldRef& p, const FieldRef
 
 }  // namespace
 
-bool hop2_supported(int ns, Sp low) { return (ns == 8 || ns == 16) && (low == Sp::F16 || low == Sp::BF16 || low == Sp::F32); }
+bool hop2_supported(int ns, Sp low, size_t vh) {
+    // 32-bit chunk indices: a half field must have fewer than 2^32 16-byte chunks
+    const size_t chunks = vh * (size_t)ns * (low == Sp::F32 ? 6 : 3);
+    return (ns == 8 || ns == 16) && (low == Sp::F16 || low == Sp::BF16 || low == Sp::F32) && chunks < (1ull << 32);
+}
 
 cudaError_t launch_hop2(const HopParams<float>& P, int kind, Sp low, Lk lk, int nsys, cudaStream_t st) {
     switch (low) {

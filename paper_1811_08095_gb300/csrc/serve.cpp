@@ -6,11 +6,14 @@
 // the loop below; client threads only enqueue and wait:
 //   1. admit queued requests, in arrival order, into free slots of their group (creating
 //      the group when the budget allows); a request that does not fit waits;
-//   2. launch `k` CG iterations on every group with running slots (asynchronous, one
-//      stream per group, so groups of different lattices overlap on the device);
-//   3. poll each group, run its FP64 reliable updates, and hand finished systems back
-//      (copy x out, free the slot); a request completes when all its systems are done;
-//   4. drop idle groups to return their memory to the budget.
+//   2. for every group whose previous chunk of iterations has finished on the device
+//      (an event query, never a blocking wait), read its systems' states, start the FP64
+//      reliable updates of parked systems, hand finished systems back (copy x out, free the
+//      slot; a request completes when all its systems are done) and launch its next chunk
+//      of `k` CG iterations.  Groups run on their own streams and progress independently,
+//      so a batch of small lattices is not held to the pace of a large one; streams of
+//      groups with less work per iteration get a higher scheduling priority;
+//   3. drop idle groups to return their memory to the budget.
 // New requests therefore enter running batches between iterations, as slots and
 // memory free up.  Caller buffers must stay valid until the ticket completes.
 #include <algorithm>
@@ -61,6 +64,8 @@ struct Group {
     std::unique_ptr<Engine> eng;
     std::unique_ptr<BatchCG> cg;
     cudaStream_t stream = nullptr;
+    cudaEvent_t ev_chunk = nullptr;  // end of the last launched chunk of iterations
+    bool in_flight = false;
     size_t reserved = 0;
     std::vector<std::shared_ptr<Request>> slot_req;  // owner of each slot
     std::vector<int> slot_rhs;
@@ -158,7 +163,16 @@ bool try_admit(serve_handle* S, const std::shared_ptr<Request>& R, std::unique_l
         g->eng = std::make_unique<Engine>();
         lk.unlock();  // device work below; the queue stays consistent (only this thread admits)
         int rc = g->eng->init(&lat, q.Ns, q.m0, q.mq, R->omega.data());
-        if (!rc && cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) rc = ODWF_ECUDA;
+        if (!rc) {
+            // less work per iteration -> higher priority (numerically lower), one level per 4x
+            int least = 0, greatest = 0;
+            cudaDeviceGetStreamPriorityRange(&least, &greatest);
+            int prio = greatest;
+            for (size_t w = sites5; w > (1u << 18) && prio < least; w >>= 2) ++prio;
+            if (cudaStreamCreateWithPriority(&g->stream, cudaStreamNonBlocking, prio) != cudaSuccess ||
+                cudaEventCreateWithFlags(&g->ev_chunk, cudaEventDisableTiming) != cudaSuccess)
+                rc = ODWF_ECUDA;
+        }
         if (!rc) rc = g->eng->set_gauge(fit->second.U, g->stream);
         odwf_solve_params prm;
         std::memset(&prm, 0, sizeof(prm));
@@ -170,6 +184,7 @@ bool try_admit(serve_handle* S, const std::shared_ptr<Request>& R, std::unique_l
         if (!rc) rc = g->cg->init(g->eng.get(), cap, prm, g->stream);
         lk.lock();
         if (rc) {
+            if (g->ev_chunk) cudaEventDestroy(g->ev_chunk);
             if (g->stream) cudaStreamDestroy(g->stream);
             complete(S, R, rc);
             return true;
@@ -208,6 +223,52 @@ bool try_admit(serve_handle* S, const std::shared_ptr<Request>& R, std::unique_l
     return true;
 }
 
+// Hand the group's finished systems back: copy x out, free the slot, complete requests
+// whose systems are all done.  Called from the worker with the serve lock released.
+void harvest(serve_handle* S, Group* g) {
+    BatchCG& cg = *g->cg;
+    for (int i = 0; i < cg.cap; ++i) {
+        if (!cg.active[i] || !cg.slot_finished(i)) continue;
+        std::shared_ptr<Request> R;
+        {
+            std::lock_guard<std::mutex> g2(S->mu);
+            R = g->slot_req[i];
+        }
+        if (!R) {
+            cg.release(i);
+            continue;
+        }
+        const int k = g->slot_rhs[i];
+        void* xo = R->x[k];
+        const size_t eb = g->eng->sites5() * 192;
+        int rc = ODWF_OK;
+        double2* dx = (double2*)xo;
+        const bool host = !is_device_ptr(xo);
+        if (host) dx = (double2*)g->eng->get_ws("serve.x", eb, &rc);
+        double tr = 0;
+        if (!rc) rc = cg.finalize(i, dx, g->stream, &tr);
+        if (!rc && host) {
+            if (cudaMemcpyAsync(xo, dx, eb, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
+                cudaStreamSynchronize(g->stream) != cudaSuccess)
+                rc = ODWF_ECUDA;
+        }
+        const int stt = cg.st_host[i].status;
+        const int iters = cg.st_host[i].iter;
+        cg.release(i);
+        std::lock_guard<std::mutex> g2(S->mu);
+        g->slot_req[i] = nullptr;
+        g->slot_rhs[i] = -1;
+        R->iters = std::max(R->iters, iters);
+        R->resid = std::max(R->resid, tr);
+        int code = rc;
+        if (!code && stt == kBreakdown) code = ODWF_EBREAKDOWN;
+        if (!code && stt != kDone) code = ODWF_ENOCONV;
+        if (code && R->status == ODWF_PENDING) R->status = code;
+        if (--R->remaining == 0) complete(S, R, R->status == ODWF_PENDING ? ODWF_OK : R->status);
+        g->last_used = Clock::now();
+    }
+}
+
 void worker_loop(serve_handle* S) {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
@@ -228,13 +289,15 @@ void worker_loop(serve_handle* S) {
             if (g->cg && g->cg->any_running()) any = true;
         if (S->stop && !any) break;
         if (!any) {
-            // 4. drop idle groups (their memory goes back to the budget), then sleep
+            // 3. drop idle groups (their memory goes back to the budget), then sleep
             for (auto it = S->groups.begin(); it != S->groups.end();) {
                 Group* g = it->get();
                 if (g->used_slots() == 0) {
                     lk.unlock();
+                    if (g->stream) cudaStreamSynchronize(g->stream);
                     g->cg.reset();
                     g->eng.reset();
+                    if (g->ev_chunk) cudaEventDestroy(g->ev_chunk);
                     if (g->stream) cudaStreamDestroy(g->stream);
                     lk.lock();
                     S->used -= std::min(S->used, g->reserved);
@@ -247,61 +310,29 @@ void worker_loop(serve_handle* S) {
             else if (!S->queue.empty()) S->cv_work.wait_for(lk, std::chrono::milliseconds(1));
             continue;
         }
-        // 2. launch iterations on every active group (async)
+        // 2. per group, without blocking: harvest a finished chunk, then launch the next one
         std::vector<Group*> act;
         for (auto& g : S->groups)
             if (g->cg && g->cg->any_running()) act.push_back(g.get());
         lk.unlock();
-        for (Group* g : act) {
-            g->cg->resume(g->stream, false);
-            g->cg->run_iterations(kIterChunk, g->stream);
-        }
-        // 3. poll, reliable updates, completions
+        bool launched = false;
         for (Group* g : act) {
             BatchCG& cg = *g->cg;
-            if (cg.poll(g->stream)) continue;
-            cg.service(g->stream);
-            for (int i = 0; i < cg.cap; ++i) {
-                if (!cg.active[i] || !cg.slot_finished(i)) continue;
-                std::shared_ptr<Request> R;
-                {
-                    std::lock_guard<std::mutex> g2(S->mu);
-                    R = g->slot_req[i];
-                }
-                if (!R) {
-                    cg.release(i);
-                    continue;
-                }
-                const int k = g->slot_rhs[i];
-                void* xo = R->x[k];
-                const size_t eb = g->eng->sites5() * 192;
-                int rc = ODWF_OK;
-                double2* dx = (double2*)xo;
-                const bool host = !is_device_ptr(xo);
-                if (host) dx = (double2*)g->eng->get_ws("serve.x", eb, &rc);
-                double tr = 0;
-                if (!rc) rc = cg.finalize(i, dx, g->stream, &tr);
-                if (!rc && host) {
-                    if (cudaMemcpyAsync(xo, dx, eb, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
-                        cudaStreamSynchronize(g->stream) != cudaSuccess)
-                        rc = ODWF_ECUDA;
-                }
-                const int stt = cg.st_host[i].status;
-                const int iters = cg.st_host[i].iter;
-                cg.release(i);
-                std::lock_guard<std::mutex> g2(S->mu);
-                g->slot_req[i] = nullptr;
-                g->slot_rhs[i] = -1;
-                R->iters = std::max(R->iters, iters);
-                R->resid = std::max(R->resid, tr);
-                int code = rc;
-                if (!code && stt == kBreakdown) code = ODWF_EBREAKDOWN;
-                if (!code && stt != kDone) code = ODWF_ENOCONV;
-                if (code && R->status == ODWF_PENDING) R->status = code;
-                if (--R->remaining == 0) complete(S, R, R->status == ODWF_PENDING ? ODWF_OK : R->status);
-                g->last_used = Clock::now();
+            if (g->in_flight) {
+                const cudaError_t q = cudaEventQuery(g->ev_chunk);
+                if (q == cudaErrorNotReady) continue;
+                g->in_flight = false;
+                if (cg.poll(g->stream)) continue;
+                cg.service(g->stream);
+                harvest(S, g);
             }
+            if (!cg.any_running()) continue;
+            cg.resume(g->stream, false);
+            cg.run_iterations(kIterChunk, g->stream);
+            if (cudaEventRecord(g->ev_chunk, g->stream) == cudaSuccess) g->in_flight = true;
+            launched = true;
         }
+        if (!launched) std::this_thread::sleep_for(std::chrono::microseconds(100));
         lk.lock();
     }
     // fail whatever is still queued
@@ -309,8 +340,10 @@ void worker_loop(serve_handle* S) {
     S->queue.clear();
     lk.unlock();
     for (auto& g : S->groups) {
+        if (g->stream) cudaStreamSynchronize(g->stream);
         g->cg.reset();
         g->eng.reset();
+        if (g->ev_chunk) cudaEventDestroy(g->ev_chunk);
         if (g->stream) cudaStreamDestroy(g->stream);
     }
     S->groups.clear();
