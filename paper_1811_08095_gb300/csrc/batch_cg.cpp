@@ -85,9 +85,12 @@ int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStr
     ODWF_CK(cudaStreamSynchronize(s));
     n_reliable.assign(cap, 0);
     upd.assign(cap, 0);
-    int prio = 0;  // the update stream takes the iteration stream's priority
-    if (s) ODWF_CK(cudaStreamGetPriority(s, &prio));
-    ODWF_CK(cudaStreamCreateWithPriority(&s_rel, cudaStreamNonBlocking, prio));
+    // The update stream runs one priority level below the iteration stream: the iterations of
+    // the other systems keep the SMs first and the FP64 update work fills in around them.
+    int prio = 0, least = 0, greatest = 0;
+    ODWF_CK(cudaStreamGetPriority(s, &prio));
+    ODWF_CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    ODWF_CK(cudaStreamCreateWithPriority(&s_rel, cudaStreamNonBlocking, prio < least ? prio + 1 : least));
     ODWF_CK(cudaEventCreateWithFlags(&ev_sync, cudaEventDisableTiming));
     bsrc.assign(cap, nullptr);
     ev_rel.assign(cap, nullptr);

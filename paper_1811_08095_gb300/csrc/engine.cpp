@@ -469,6 +469,40 @@ static int check_params(const odwf_solve_params* prm) {
     return ODWF_OK;
 }
 
+namespace {
+// An internal stream of the highest priority that starts after the work queued on the
+// caller's stream and that the caller's stream waits for at the end.
+struct SolveStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    int open(cudaStream_t user) {
+        int least = 0, greatest = 0;
+        ODWF_CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        ODWF_CK(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest));
+        ODWF_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        ODWF_CK(cudaEventRecord(ev, user));
+        ODWF_CK(cudaStreamWaitEvent(s, ev, 0));
+        return ODWF_OK;
+    }
+    int close(cudaStream_t user) {
+        int rc = ODWF_OK;
+        if (s && ev) {
+            if (cudaEventRecord(ev, s) != cudaSuccess || cudaStreamWaitEvent(user, ev, 0) != cudaSuccess)
+                rc = fail(ODWF_ECUDA, "solve: joining the caller's stream failed");
+        }
+        if (ev) cudaEventDestroy(ev);
+        if (s) cudaStreamDestroy(s);  // released once its queued work has completed
+        s = nullptr;
+        ev = nullptr;
+        return rc;
+    }
+    ~SolveStream() {
+        if (ev) cudaEventDestroy(ev);
+        if (s) cudaStreamDestroy(s);
+    }
+};
+}  // namespace
+
 int Engine::solve(int nsys, void* const* x, const void* const* b, const double* mq_arr,
                   const odwf_solve_params* prm, odwf_solve_stats* stats, cudaStream_t st) {
     int rc = check_params(prm);
@@ -482,6 +516,21 @@ int Engine::solve(int nsys, void* const* x, const void* const* b, const double* 
         return solve_full(x[0], b[0], prm, stats, st);
     }
     const auto t0 = std::chrono::steady_clock::now();
+    // The solve runs on an internal stream of the highest priority (its reliable updates one
+    // level below), joined to the caller's stream at both ends.
+    SolveStream ss;
+    if ((rc = ss.open(st))) return rc;
+    rc = solve_on(nsys, x, b, mq_arr, prm, stats, ss.s);
+    const int rc2 = ss.close(st);
+    if (stats)
+        for (int i = 0; i < nsys; ++i)
+            stats[i].time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return rc ? rc : rc2;
+}
+
+int Engine::solve_on(int nsys, void* const* x, const void* const* b, const double* mq_arr,
+                     const odwf_solve_params* prm, odwf_solve_stats* stats, cudaStream_t st) {
+    int rc = 0;
     BatchCG bc;
     if ((rc = bc.init(this, nsys, *prm, st))) return rc;
     const size_t eb = ext_bytes(ODWF_MODE_SCHUR_EVEN);
@@ -520,9 +569,6 @@ int Engine::solve(int nsys, void* const* x, const void* const* b, const double* 
             stats[i].status = code;
         }
     }
-    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    if (stats)
-        for (int i = 0; i < nsys; ++i) stats[i].time_ms = ms;
     if (first_bad == ODWF_ENOCONV) set_error("solve: max_iter reached before the tolerance");
     if (first_bad == ODWF_EBREAKDOWN) set_error("solve: CG breakdown");
     return first_bad;

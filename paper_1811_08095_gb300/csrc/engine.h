@@ -100,6 +100,8 @@ struct Engine {
     int apply_low_normal(void* out, const void* in, int prec, int recon, cudaStream_t st);
     int solve(int nsys, void* const* x, const void* const* b, const double* mq_arr, const odwf_solve_params* prm,
               odwf_solve_stats* stats, cudaStream_t st);
+    int solve_on(int nsys, void* const* x, const void* const* b, const double* mq_arr,
+                 const odwf_solve_params* prm, odwf_solve_stats* stats, cudaStream_t st);
     int solve_full(void* x, const void* b, const odwf_solve_params* prm, odwf_solve_stats* stats,
                    cudaStream_t st);
 };

@@ -361,16 +361,12 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
     float nrm = 0.f;  // per-thread partial sums in FP32, FP64 across warps and blocks (block_sum)
     if (KIND == K1) {
         // chi_t = B M^-1 (-1/2 y)
-#pragma unroll
-        for (int k = 0; k < 24; ++k) acc[k] *= -0.5f;
-        minv_apply(acc, cf, r, s, NS, false);
+        minv_apply_f<false>(acc, cf, r, s, NS, false, -0.5f);
         bidiag_apply(acc, cf.rho[s], cf.sigma[s], r, s, NS, false);
         if (valid) SpinorIO<SP, float>::store(P.out.d(sys), P.out.n(sys), (size_t)h, s, NS, acc);
     } else if (KIND == K2) {
         // s = p - M^-1 (-1/2 y) = p + M^-1 (y/2);  |s|^2;  a = M^-dag s
-#pragma unroll
-        for (int k = 0; k < 24; ++k) acc[k] *= 0.5f;
-        minv_apply(acc, cf, r, s, NS, false);
+        minv_apply_f(acc, cf, r, s, NS, false, 0.5f);
         float z[24];
         if (valid) {
             SpinorIO<SP, float>::load(P.z.d(sys), P.z.n(sys), (size_t)h, s, NS, z);
@@ -383,14 +379,12 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
             acc[k] += z[k];
             nrm = fmaf(acc[k], acc[k], nrm);
         }
-        minv_apply(acc, cf, r, s, NS, true);
+        minv_apply_f(acc, cf, r, s, NS, true, 1.f);
         if (valid) SpinorIO<SP, float>::store(P.out.d(sys), P.out.n(sys), (size_t)h, s, NS, acc);
     } else if (KIND == K3) {
         // c = M^-dag (-1/2 B^dag y)
         bidiag_apply(acc, cf.rho[s], cf.sigma[s], r, s, NS, true);
-#pragma unroll
-        for (int k = 0; k < 24; ++k) acc[k] *= -0.5f;
-        minv_apply(acc, cf, r, s, NS, true);
+        minv_apply_f(acc, cf, r, s, NS, true, -0.5f);
         if (valid) SpinorIO<SP, float>::store(P.out.d(sys), P.out.n(sys), (size_t)h, s, NS, acc);
     } else {
         // A p = M^dag a + 1/2 B^dag y;  r -= alpha A p;  x += alpha p

@@ -316,6 +316,81 @@ __device__ __forceinline__ void minv_apply(R v[24], const Coef5<R>& cf, R r, int
     }
 }
 
+// FP32 form of cyclic_solve12 for the mixed-precision kernels: the same scan, with the
+// 12 reals handled as six FP32x2 pairs (one packed FMA per pair and step) and an extra
+// factor `pre` folded into the 1/d_s scaling (v <- pre v before the solve).
+template <bool PACK>
+__device__ __forceinline__ void cyclic_solve12_f(float v[12], float pre, float inv_d, float c_s, float r, int s,
+                                                 int ns, bool forward) {
+    if (!PACK) {  // scalar FMAs (fewer register-pair constraints where registers are tight)
+        float coef = -c_s * inv_d;
+        const float sc = pre * inv_d;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] *= sc;
+        const int q = forward ? s : ns - 1 - s;
+        for (int off = 1; off < ns; off <<= 1) {
+            const float pc = forward ? shfl_up(coef, off, ns) : shfl_down(coef, off, ns);
+            const float cm = q >= off ? coef : 0.f;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                const float pv = forward ? shfl_up(v[k], off, ns) : shfl_down(v[k], off, ns);
+                v[k] = fmaf(cm, pv, v[k]);
+            }
+            if (q >= off) coef *= pc;
+        }
+        const int last = forward ? ns - 1 : 0;
+        const float Al = shfl_idx(coef, last, ns);
+        const float cf = coef * (-r / (1.f + r * Al));
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = fmaf(cf, shfl_idx(v[k], last, ns), v[k]);
+        return;
+    }
+    float coef = -c_s * inv_d;
+    const float sc = pre * inv_d;
+    float2 w[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] = make_float2(v[2 * k] * sc, v[2 * k + 1] * sc);
+    const int q = forward ? s : ns - 1 - s;
+    for (int off = 1; off < ns; off <<= 1) {
+        const float pc = forward ? shfl_up(coef, off, ns) : shfl_down(coef, off, ns);
+        const float cm = q >= off ? coef : 0.f;
+        const float2 cm2 = make_float2(cm, cm);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float2 pv;
+            pv.x = forward ? shfl_up(w[k].x, off, ns) : shfl_down(w[k].x, off, ns);
+            pv.y = forward ? shfl_up(w[k].y, off, ns) : shfl_down(w[k].y, off, ns);
+            w[k] = __ffma2_rn(cm2, pv, w[k]);
+        }
+        if (q >= off) coef *= pc;
+    }
+    const int last = forward ? ns - 1 : 0;
+    const float Al = shfl_idx(coef, last, ns);
+    const float cf = coef * (-r / (1.f + r * Al));
+    const float2 cf2 = make_float2(cf, cf);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float2 gl = make_float2(shfl_idx(w[k].x, last, ns), shfl_idx(w[k].y, last, ns));
+        w[k] = __ffma2_rn(cf2, gl, w[k]);
+        v[2 * k] = w[k].x;
+        v[2 * k + 1] = w[k].y;
+    }
+}
+
+// M^-1 / M^-dag (as minv_apply) of pre * v, FP32
+template <bool PACK = true>
+__device__ __forceinline__ void minv_apply_f(float v[24], const Coef5<float>& cf, float r, int s, int ns, bool dag,
+                                             float pre) {
+    const float inv_d = cf.inv_d[s];
+    if (!dag) {
+        cyclic_solve12_f<PACK>(v, pre, inv_d, cf.e[s], r, s, ns, true);
+        cyclic_solve12_f<PACK>(v + 12, pre, inv_d, cf.e[s], r, s, ns, false);
+    } else {
+        cyclic_solve12_f<PACK>(v, pre, inv_d, cf.e[(s + 1) & (ns - 1)], r, s, ns, false);
+        cyclic_solve12_f<PACK>(v + 12, pre, inv_d, cf.e[(s + ns - 1) & (ns - 1)], r, s, ns, true);
+    }
+}
+
 // ---------------------------------------------------------------- CG scalar state (device)
 // kRestarting: a reliable update has recomputed the residual and restarted the inner
 // iteration on the update stream; the iteration stream switches it back to kRunning once
