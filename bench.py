@@ -206,7 +206,7 @@ def run_ours(args, world, rank, local):
 
     def step(prec):
         return h.cg_solve_batched(xs, bs, list(MASSES), tol=TOL, max_iter=200000, prec=prec, delta=args.delta,
-                                  link_recon=args.link_recon, stream=stream)
+                                  link_recon=args.link_recon, check_every=args.check_every, stream=stream)
 
     for _ in range(args.warmup):
         stats = step(args.prec)
@@ -635,6 +635,7 @@ def main():
     ap.add_argument("--prec", default="f16", choices=["f16", "bf16", "f32"])
     ap.add_argument("--delta", type=float, default=0.01, help="reliable-update threshold")
     ap.add_argument("--link-recon", type=int, default=12, choices=[12, 18])
+    ap.add_argument("--check-every", type=int, default=8, help="iterations between host polls of the solver state")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "serve"],
                     help="c2: the default line; c3: 36-system batch on 24^3x48; c5: one 64^4 solve; serve")
     ap.add_argument("--rate", type=float, default=50.0, help="serve: arrivals per second")

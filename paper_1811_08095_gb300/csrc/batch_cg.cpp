@@ -1,12 +1,21 @@
 // Slot-based batched CG (see batch_cg.h).
 #include "batch_cg.h"
 
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 namespace odwf {
 
+void BatchCG::drop_graphs() {
+    for (auto& kv : graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    graphs.clear();
+}
+
 BatchCG::~BatchCG() {
+    drop_graphs();
     if (s_rel) cudaStreamSynchronize(s_rel);
     for (cudaEvent_t e : ev_rel)
         if (e) cudaEventDestroy(e);
@@ -34,7 +43,7 @@ HopParams<float> BatchCG::params<float>(int p_out) const {
     return P;
 }
 
-int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStream_t s) {
+int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStream_t s, int update_prio_drop) {
     E = e;
     cap = capacity;
     mixed = prm.prec != ODWF_F64;
@@ -85,12 +94,10 @@ int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStr
     ODWF_CK(cudaStreamSynchronize(s));
     n_reliable.assign(cap, 0);
     upd.assign(cap, 0);
-    // The update stream runs one priority level below the iteration stream: the iterations of
-    // the other systems keep the SMs first and the FP64 update work fills in around them.
     int prio = 0, least = 0, greatest = 0;
     ODWF_CK(cudaStreamGetPriority(s, &prio));
     ODWF_CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-    ODWF_CK(cudaStreamCreateWithPriority(&s_rel, cudaStreamNonBlocking, prio < least ? prio + 1 : least));
+    ODWF_CK(cudaStreamCreateWithPriority(&s_rel, cudaStreamNonBlocking, std::min(least, prio + update_prio_drop)));
     ODWF_CK(cudaEventCreateWithFlags(&ev_sync, cudaEventDisableTiming));
     bsrc.assign(cap, nullptr);
     ev_rel.assign(cap, nullptr);
@@ -225,6 +232,41 @@ int BatchCG::run_iterations(int k, cudaStream_t s) {
         }
     if (hi < 0) return ODWF_OK;
     const int n = hi - lo + 1;
+    // direct launches while profiling (per-launch events), on the default streams (not
+    // capturable), or when ODWF_GRAPHS=0 is set in the environment
+    static const bool graphs_on = [] {
+        const char* v = std::getenv("ODWF_GRAPHS");
+        return !(v && v[0] == '0');
+    }();
+    if (!graphs_on || prof_enabled() || s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread)
+        return launch_iterations(k, lo, n, s);
+    const unsigned long long key = ((unsigned long long)lo << 40) | ((unsigned long long)n << 20) | (unsigned)k;
+    auto it = graphs.find(key);
+    if (it == graphs.end()) {
+        if (graphs.size() >= 32) drop_graphs();
+        const long long c0 = launch_count();
+        ODWF_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const int rc = launch_iterations(k, lo, n, s);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(s, &g);
+        GraphEntry e;
+        e.kernels = launch_count() - c0;
+        note_launches(-e.kernels);  // captured, not launched
+        if (rc || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return rc ? rc : cuda_fail(ce, "cudaStreamEndCapture(CG iterations)");
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&e.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate(CG iterations)");
+        it = graphs.emplace(key, e).first;
+    }
+    ODWF_CK(cudaGraphLaunch(it->second.exec, s));
+    note_launches(it->second.kernels);
+    return ODWF_OK;
+}
+
+int BatchCG::launch_iterations(int k, int lo, int n, cudaStream_t s) {
     const size_t n5 = E->sites5();
     for (int it = 0; it < k; ++it) {
         if (!mixed) {

@@ -25,6 +25,7 @@
 #pragma once
 
 #include <chrono>
+#include <map>
 #include <vector>
 
 #include "engine.h"
@@ -67,11 +68,21 @@ struct BatchCG {
     cudaEvent_t ev_sync = nullptr;     // orders the shared FP64 buffers between the two streams
     std::vector<double> mq;
     std::vector<double> slot_tol;
+    // A chunk of k iterations over slots lo..lo+n-1 is captured once into a CUDA graph and
+    // replayed (launch-bound small lattices; not while the kernel profiler is enabled).
+    struct GraphEntry {
+        cudaGraphExec_t exec = nullptr;
+        long long kernels = 0;
+    };
+    std::map<unsigned long long, GraphEntry> graphs;
     int pcls[5] = {-1, -1, -1, -1, -1};  // profiler classes: K1..K4, p update
     int pcls_rel[4] = {-1, -1, -1, -1};  // FP64 residual hops of the reliable update
 
     ~BatchCG();
-    int init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStream_t s);
+    // update_prio_drop: priority levels of the update stream below the iteration stream s
+    // (1 in a single batch, so that the other systems' iterations keep the SMs first; 0 in
+    // the serving loop, where a group's updates must not fall below other groups' iterations)
+    int init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStream_t s, int update_prio_drop = 0);
     // b_ext: even-site external field (complex128).  A device pointer is read again at every
     // reliable update (mixed precision) and must stay valid until finalize(); a host pointer is
     // copied.  tol_slot / max_iter_slot <= 0 keep the batch defaults.
@@ -92,6 +103,8 @@ struct BatchCG {
     template <class R>
     HopParams<R> params(int p_out) const;
     int fp64_residual(int slot, cudaStream_t s);
+    int launch_iterations(int k, int lo, int n, cudaStream_t s);
+    void drop_graphs();
     FieldRef Rref() const { return mixed ? R64.ref_shared() : R64.ref(); }
     FieldRef Bref() const { return mixed ? B64.ref_shared() : B64.ref(); }
     int load_b(int slot, cudaStream_t s);               // mixed: pack the slot's b into the shared B64

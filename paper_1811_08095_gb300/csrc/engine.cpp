@@ -532,7 +532,7 @@ int Engine::solve_on(int nsys, void* const* x, const void* const* b, const doubl
                      const odwf_solve_params* prm, odwf_solve_stats* stats, cudaStream_t st) {
     int rc = 0;
     BatchCG bc;
-    if ((rc = bc.init(this, nsys, *prm, st))) return rc;
+    if ((rc = bc.init(this, nsys, *prm, st, 1))) return rc;
     const size_t eb = ext_bytes(ODWF_MODE_SCHUR_EVEN);
     for (int i = 0; i < nsys; ++i) {
         double m = mq;

@@ -280,10 +280,8 @@ __device__ __forceinline__ void reduce_and_finalize(R v, double* partials, unsig
 }
 
 // ---------------------------------------------------------------- the fused hopping kernel
-// FP64: at most 128 registers, so that two blocks (16 warps) share an SM and hide the FP64
-// pipe's latency (unbounded, the FP64 variants take 144-182 registers: one block per SM).
 template <class SPin, class SPz, class SPout, class SPacc, class LK, class R, int F>
-__global__ void __launch_bounds__(256, (sizeof(R) == 8) ? 2 : 1) hop_kernel(const HopParams<R> P) {
+__global__ void __launch_bounds__(256) hop_kernel(const HopParams<R> P) {
     constexpr bool DAG = (F & F_DAG) != 0;
     constexpr int ZOP = (F & F_ZOP_MASK) >> F_ZOP_SHIFT;
     constexpr int HOPOP = (F & F_HOP_MASK) >> F_HOP_SHIFT;

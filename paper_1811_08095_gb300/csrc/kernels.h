@@ -88,6 +88,7 @@ int lg2(int v);
 // process-wide count of kernel launches issued by the library
 void note_launch();
 long long launch_count();
+void note_launches(long long n);  // adjusts the count (graph replays: kernels per graph)
 inline int blocks_for(size_t n, int bs) { return (int)((n + bs - 1) / bs); }
 
 }  // namespace odwf
