@@ -25,79 +25,7 @@ namespace {
 
 constexpr int kBS2 = 256;
 
-// raw stored values (not scaled) and the scale of one 5D site
-template <class SP>
-struct RawIO;
-
-template <>
-struct RawIO<SpF32> {
-    static __device__ __forceinline__ float load(const void* base, const float*, size_t h, int s, int ns, float v[24]) {
-        const float4* p = reinterpret_cast<const float4*>(base);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const float4 q = __ldg(p + chunk_off(h, k, 6, ns, s));
-            v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
-        }
-        return 1.f;
-    }
-};
-
-template <class H2>
-struct RawHalfIO {
-    static __device__ __forceinline__ float load(const void* base, const float* norm, size_t h, int s, int ns,
-                                                 float v[24]) {
-        const uint4* p = reinterpret_cast<const uint4*>(base);
-        const float sc = __ldg(norm + h * ns + s);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const uint4 q = __ldg(p + chunk_off(h, k, 3, ns, s));
-            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                H2 hv;
-                *reinterpret_cast<uint32_t*>(&hv) = w[j];
-                const float2 f = Half2Cvt<H2>::to_f2(hv);
-                v[8 * k + 2 * j] = f.x;
-                v[8 * k + 2 * j + 1] = f.y;
-            }
-        }
-        return sc;
-    }
-};
-template <>
-struct RawIO<SpF16> : RawHalfIO<__half2> {};
-template <>
-struct RawIO<SpBF16> : RawHalfIO<__nv_bfloat162> {};
-
 enum { K1 = 1, K2 = 2, K3 = 3, K4 = 4 };
-
-// acc += m_up * w (upper spins) and acc_dn += m_dn * G^dag w (lower spins)
-__device__ __forceinline__ void accumulate_scaled(int mu, float m_up, float m_dn, const float w[12], float acc[24]) {
-    const float* w0 = w;
-    const float* w1 = w + 6;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        acc[2 * c] = fmaf(m_up, w0[2 * c], acc[2 * c]);
-        acc[2 * c + 1] = fmaf(m_up, w0[2 * c + 1], acc[2 * c + 1]);
-        acc[6 + 2 * c] = fmaf(m_up, w1[2 * c], acc[6 + 2 * c]);
-        acc[6 + 2 * c + 1] = fmaf(m_up, w1[2 * c + 1], acc[6 + 2 * c + 1]);
-        float l0r, l0i, l1r, l1i;
-        switch (mu) {
-            case 0: l0r = -w1[2 * c + 1]; l0i = w1[2 * c]; l1r = -w0[2 * c + 1]; l1i = w0[2 * c]; break;
-            case 1: l0r = w1[2 * c]; l0i = w1[2 * c + 1]; l1r = -w0[2 * c]; l1i = -w0[2 * c + 1]; break;
-            case 2: l0r = -w0[2 * c + 1]; l0i = w0[2 * c]; l1r = w1[2 * c + 1]; l1i = -w1[2 * c]; break;
-            default: l0r = w0[2 * c]; l0i = w0[2 * c + 1]; l1r = w1[2 * c]; l1i = w1[2 * c + 1]; break;
-        }
-        acc[12 + 2 * c] = fmaf(m_dn, l0r, acc[12 + 2 * c]);
-        acc[12 + 2 * c + 1] = fmaf(m_dn, l0i, acc[12 + 2 * c + 1]);
-        acc[18 + 2 * c] = fmaf(m_dn, l1r, acc[18 + 2 * c]);
-        acc[18 + 2 * c + 1] = fmaf(m_dn, l1i, acc[18 + 2 * c + 1]);
-    }
-}
-
-// Unscaled projection h = v^up + sg G v^dn (the scale is applied at accumulation)
-__device__ __forceinline__ void project_raw(int mu, float sg, const float v[24], float h[12]) { project(mu, sg, v, h); }
-
 
 // ---------------------------------------------------------------- packed FP32 pairs
 // A "spin pair" holds one colour and one real/imaginary part of the two spins of a
@@ -174,7 +102,7 @@ __device__ __forceinline__ void unpack_site(const RawSite<SP>& r, float2 Ur[3], 
 // accumulated in AD (order (2, 3)) for mu = 2, 3 and in ADS (order (3, 2)) for mu = 0, 1, so
 // that no pair ever needs its halves exchanged.  The link comes from shared memory as nine
 // float4 (ur, ur, ui, ui), element (a, b) at index 3a + b.
-// Link sources for hop_dir_packed: element (a, b) of U as broadcast pairs (ur, ur), (ui, ui).
+// Link source for hop_dir_packed: element (a, b) of U as broadcast pairs (ur, ur), (ui, ui).
 struct LinkStaged {  // nine float4 (ur, ur, ui, ui) in shared memory
     const float4* q;
     __device__ __forceinline__ void get(int a, int b, float2& ur, float2& ui) const {
@@ -183,14 +111,6 @@ struct LinkStaged {  // nine float4 (ur, ur, ui, ui) in shared memory
         ui = make_float2(v.z, v.w);
     }
 };
-struct LinkRegs {  // 18 reals held in registers
-    float u[18];
-    __device__ __forceinline__ void get(int a, int b, float2& ur, float2& ui) const {
-        ur = make_float2(u[2 * (3 * a + b)], u[2 * (3 * a + b)]);
-        ui = make_float2(u[2 * (3 * a + b) + 1], u[2 * (3 * a + b) + 1]);
-    }
-};
-
 template <class SP, int MU, bool DAGU, class LF>
 __device__ __forceinline__ void hop_dir_packed(const RawSite<SP>& raw, float sc_sign, float sg, const LF& lnk,
                                                float2 AUr[3], float2 AUi[3], float2 ADr[3], float2 ADi[3],
@@ -264,7 +184,7 @@ __device__ __forceinline__ void hop_dir_packed(const RawSite<SP>& raw, float sc_
 constexpr int kLinkStride = 36;                  // floats per staged link: 9 x (ur, ur, ui, ui)
 constexpr int kSiteLinks = 8 * kLinkStride + 4;  // floats per site (padding spreads banks)
 
-template <class SP, class LK, int NS, int KIND, bool GL>
+template <class SP, class LK, int NS, int KIND>
 __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P) {
     constexpr bool DAG = (KIND == K3 || KIND == K4);
     const int sys = blockIdx.y + P.sys_base;
@@ -294,9 +214,9 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
     }
 
     // stage the site's eight links in shared memory: lane d < 8 of the group loads direction d
-    __shared__ __align__(16) float s_links[GL ? 4 : (kBS2 / NS) * kSiteLinks];
-    float* my_links = s_links + (GL ? 0 : (threadIdx.x / NS) * kSiteLinks);
-    if (!GL && s < 8) {
+    __shared__ __align__(16) float s_links[(kBS2 / NS) * kSiteLinks];
+    float* my_links = s_links + (threadIdx.x / NS) * kSiteLinks;
+    if (s < 8) {
         const int mu = s >> 1, dir = s & 1;
         const size_t lidx = dir == 0 ? ((size_t)(p_out * 4 + mu) * P.g.Vh + h)
                                      : ((size_t)(p_in * 4 + mu) * P.g.Vh + nb[s]);
@@ -310,14 +230,12 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
 
     const void* in = P.in.d(sys);
     const float* in_n = P.in.n(sys);
-    (void)&project_raw;
     float2 AUr[3], AUi[3], ADr[3], ADi[3], ADSr[3], ADSi[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) AUr[c] = AUi[c] = ADr[c] = ADi[c] = ADSr[c] = ADSi[c] = make_float2(0.f, 0.f);
     const float4* L4 = reinterpret_cast<const float4*>(my_links);
     // forward hops use (1 - gamma) for D and (1 + gamma) for D^dag; backward the opposite
     constexpr float SF = DAG ? 1.f : -1.f;
-    // links: staged in shared memory, or (GL) loaded per lane with broadcast global loads
     // neighbour j + 1 is fetched before neighbour j is processed
     RawSite<SP> rs[2];
     fetch_site<SP>(in, in_n, (unsigned)nb[0], s, NS, valid, rs[0]);
@@ -326,18 +244,9 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
         constexpr int j_ = 2 * MU_ + DIR_;                                                                        \
         if (j_ < 7) fetch_site<SP>(in, in_n, (unsigned)nb[j_ + 1 < 8 ? j_ + 1 : 7], s, NS, valid, rs[(j_ + 1) & 1]); \
         const float sgn_ = (flip & (1u << j_)) ? -1.f : 1.f;                                                     \
-        if (GL) {                                                                                                 \
-            LinkRegs lr_;                                                                                         \
-            const size_t lidx_ = DIR_ == 0 ? ((size_t)(p_out * 4 + MU_) * P.g.Vh + h)                             \
-                                           : ((size_t)(p_in * 4 + MU_) * P.g.Vh + nb[j_]);                        \
-            LinkIO<LK, float>::load(P.links, lidx_, lr_.u);                                                      \
-            hop_dir_packed<SP, MU_, DIR_ == 1>(rs[j_ & 1], sgn_, DIR_ == 0 ? SF : -SF, lr_, AUr, AUi, ADr, ADi,    \
-                                               ADSr, ADSi);                                                       \
-        } else {                                                                                                  \
-            const LinkStaged ls_{L4 + j_ * 9};                                                                    \
-            hop_dir_packed<SP, MU_, DIR_ == 1>(rs[j_ & 1], sgn_, DIR_ == 0 ? SF : -SF, ls_, AUr, AUi, ADr, ADi,    \
-                                               ADSr, ADSi);                                                       \
-        }                                                                                                         \
+        const LinkStaged ls_{L4 + j_ * 9};                                                                        \
+        hop_dir_packed<SP, MU_, DIR_ == 1>(rs[j_ & 1], sgn_, DIR_ == 0 ? SF : -SF, ls_, AUr, AUi, ADr, ADi, ADSr,  \
+                                           ADSi);                                                                 \
     }
     ODWF_HOP_DIR(0, 0); ODWF_HOP_DIR(0, 1);
     ODWF_HOP_DIR(1, 0); ODWF_HOP_DIR(1, 1);
@@ -452,20 +361,16 @@ __global__ void __launch_bounds__(kBS2) p_update2_kernel(FieldRef rr, FieldRef p
     if (valid) SpinorIO<SP, float>::store(chi.d(sys), chi.n(sys), h, s, NS, v);
 }
 
-#ifndef ODWF_HOP2_GLOBAL_LINKS
-#define ODWF_HOP2_GLOBAL_LINKS 0
-#endif
 template <class SP, class LK, int NS>
 cudaError_t hop2_k(const HopParams<float>& P, int kind, int nsys, cudaStream_t st) {
-    constexpr bool GL = ODWF_HOP2_GLOBAL_LINKS != 0;
     const size_t n = (size_t)P.g.Vh * NS;
     dim3 grid(blocks_for(n, kBS2), nsys);
     note_launch();
     switch (kind) {
-        case K1: hop2_kernel<SP, LK, NS, K1, GL><<<grid, kBS2, 0, st>>>(P); break;
-        case K2: hop2_kernel<SP, LK, NS, K2, GL><<<grid, kBS2, 0, st>>>(P); break;
-        case K3: hop2_kernel<SP, LK, NS, K3, GL><<<grid, kBS2, 0, st>>>(P); break;
-        default: hop2_kernel<SP, LK, NS, K4, GL><<<grid, kBS2, 0, st>>>(P); break;
+        case K1: hop2_kernel<SP, LK, NS, K1><<<grid, kBS2, 0, st>>>(P); break;
+        case K2: hop2_kernel<SP, LK, NS, K2><<<grid, kBS2, 0, st>>>(P); break;
+        case K3: hop2_kernel<SP, LK, NS, K3><<<grid, kBS2, 0, st>>>(P); break;
+        default: hop2_kernel<SP, LK, NS, K4><<<grid, kBS2, 0, st>>>(P); break;
     }
     return cudaGetLastError();
 }
