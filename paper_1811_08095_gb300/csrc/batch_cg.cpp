@@ -270,18 +270,24 @@ int BatchCG::launch_iterations(int k, int lo, int n, cudaStream_t s) {
     const size_t n5 = E->sites5();
     for (int it = 0; it < k; ++it) {
         if (!mixed) {
+            // as in the reliable update: the non-dagger hops read chi = B psi, shifted once per
+            // site into C64 (free until the third hop writes it)
+            ODWF_CK(launch_m5_f64(P64.ref(), C64.ref(), E->vh(), E->ns, r_dev, lo, n, 4, E->cf64, s, st, kRunning));
             auto P = params<double>(1);
             P.gate = 1;
             P.need_status = kRunning;
             P.sys_base = lo;
-            P.in = P64.ref();
+            P.preshifted = 1;
+            P.in = C64.ref();
             P.out = T64.ref();
             { auto pb_ = prof_begin(pcls[0], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_f64(P, Epi::MINV, n, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+            ODWF_CK(launch_m5_f64(T64.ref(), C64.ref(), E->vh(), E->ns, r_dev, lo, n, 4, E->cf64, s, st, kRunning));
             P.p_out = 0;
-            P.in = T64.ref();
+            P.in = C64.ref();
             P.z = P64.ref();
             P.out = A64.ref();
             { auto pb_ = prof_begin(pcls[1], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_f64(P, Epi::SCHUR_NORM_MDINV, n, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+            P.preshifted = 0;
             P.p_out = 1;
             P.in = A64.ref();
             P.z = FieldRef{};

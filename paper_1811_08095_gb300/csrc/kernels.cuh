@@ -422,11 +422,13 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams<R> P) {
 }
 
 // ---------------------------------------------------------------- site-local kernels
-// out = op(in) with op in {M, M^dag, M^-1, M^-dag} on n_sites * Ns 5D sites (lane groups of Ns)
+// out = op(in) with op in {M, M^dag, M^-1, M^-dag, B} on n_sites * Ns 5D sites (lane groups of Ns)
 template <class SPin, class SPout, class R>
 __global__ void __launch_bounds__(256) m5_kernel(FieldRef in, FieldRef out, size_t n_sites, int ns, int lg_ns,
-                                                 const double* r_sys, int sys_base, int op, Coef5<R> cf) {
+                                                 const double* r_sys, int sys_base, int op, Coef5<R> cf,
+                                                 const SysState* gate_st, int need) {
     const int sys = blockIdx.y + sys_base;
+    if (gate_st && gate_st[sys].status != need) return;  // optional: only systems with this status
     const size_t gi = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int s = (int)(gi & (size_t)(ns - 1));
     const size_t h = gi >> lg_ns;

@@ -51,8 +51,10 @@ cudaError_t launch_p_update2(Sp low, int ns, const FieldRef& r, const FieldRef& 
                              cudaStream_t stream);
 
 // Site-local M, M^dag, M^-1, M^-dag (op 0..3); op 4 = B (the chiral shift rho + sigma L)
+// gate_st (optional): only systems whose status equals `need` are processed
 cudaError_t launch_m5_f64(const FieldRef& in, const FieldRef& out, size_t n_sites, int ns, const double* r_sys,
-                          int sys_base, int nsys, int op, const Coef5<double>& cf, cudaStream_t st);
+                          int sys_base, int nsys, int op, const Coef5<double>& cf, cudaStream_t st,
+                          const SysState* gate_st = nullptr, int need = 0);
 cudaError_t launch_m5_mixed(Sp low, const FieldRef& in, const FieldRef& out, size_t n_sites, int ns,
                             const double* r_sys, int sys_base, int nsys, int op, const Coef5<float>& cf,
                             cudaStream_t st);

@@ -53,9 +53,12 @@ cudaError_t launch_hop_f64(const HopParams<double>& P, Epi e, int nsys, cudaStre
 }
 
 cudaError_t launch_m5_f64(const FieldRef& in, const FieldRef& out, size_t n_sites, int ns, const double* r_sys,
-                          int sys_base, int nsys, int op, const Coef5<double>& cf, cudaStream_t st) {
+                          int sys_base, int nsys, int op, const Coef5<double>& cf, cudaStream_t st,
+                          const SysState* gate_st, int need) {
     dim3 grid(blocks_for(n_sites * ns, kBS), nsys);
-    note_launch(); m5_kernel<SpF64, SpF64, double><<<grid, kBS, 0, st>>>(in, out, n_sites, ns, lg2(ns), r_sys, sys_base, op, cf);
+    note_launch();
+    m5_kernel<SpF64, SpF64, double><<<grid, kBS, 0, st>>>(in, out, n_sites, ns, lg2(ns), r_sys, sys_base, op, cf,
+                                                           gate_st, need);
     return cudaGetLastError();
 }
 

@@ -54,9 +54,9 @@ cudaError_t launch_m5_mixed(Sp low, const FieldRef& in, const FieldRef& out, siz
     dim3 grid(blocks_for(n_sites * ns, kBS), nsys);
     const int lg = lg2(ns);
     switch (low) {
-        case Sp::F32: note_launch(); m5_kernel<SpF32, SpF32, float><<<grid, kBS, 0, st>>>(in, out, n_sites, ns, lg, r_sys, sys_base, op, cf); break;
-        case Sp::F16: note_launch(); m5_kernel<SpF16, SpF16, float><<<grid, kBS, 0, st>>>(in, out, n_sites, ns, lg, r_sys, sys_base, op, cf); break;
-        case Sp::BF16: note_launch(); m5_kernel<SpBF16, SpBF16, float><<<grid, kBS, 0, st>>>(in, out, n_sites, ns, lg, r_sys, sys_base, op, cf); break;
+        case Sp::F32: note_launch(); m5_kernel<SpF32, SpF32, float><<<grid, kBS, 0, st>>>(in, out, n_sites, ns, lg, r_sys, sys_base, op, cf, nullptr, 0); break;
+        case Sp::F16: note_launch(); m5_kernel<SpF16, SpF16, float><<<grid, kBS, 0, st>>>(in, out, n_sites, ns, lg, r_sys, sys_base, op, cf, nullptr, 0); break;
+        case Sp::BF16: note_launch(); m5_kernel<SpBF16, SpBF16, float><<<grid, kBS, 0, st>>>(in, out, n_sites, ns, lg, r_sys, sys_base, op, cf, nullptr, 0); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -114,7 +114,7 @@ extern "C" int odwf_apply_m5_noalloc(int Ns, double m0, double mq, const double*
     note_launch();
     pack_kernel<SpF64><<<grid, bs, 0, st>>>((const double2*)in, X, gf, 0, Ns, lg, 1);
     note_launch();
-    m5_kernel<SpF64, SpF64, double><<<dim3(grid, 1), bs, 0, st>>>(X, Y, (size_t)n_sites, Ns, lg, r_dev, 0, op, cf);
+    m5_kernel<SpF64, SpF64, double><<<dim3(grid, 1), bs, 0, st>>>(X, Y, (size_t)n_sites, Ns, lg, r_dev, 0, op, cf, nullptr, 0);
     note_launch();
     unpack_kernel<SpF64><<<grid, bs, 0, st>>>(Y, (double2*)out, gf, 0, Ns, lg, 1);
     cudaError_t e = cudaGetLastError();
