@@ -209,6 +209,9 @@ int odwf_apply_m5_noalloc(int Ns, double m0, double mq, const double* omega, voi
 /*
  * Solve one system by conjugate gradient (Sec. 2).  x: initial guess ignored, result
  * written; b: right-hand side (layouts by system).  stats may be NULL.
+ * The solve runs on an internal stream joined to `stream` at both ends and returns when it
+ * has finished.  Chunks of iterations are replayed as CUDA graphs unless the kernel profiler
+ * is enabled or the environment sets ODWF_GRAPHS=0.
  * Returns ODWF_OK on convergence to params->tol, ODWF_ENOCONV at max_iter (x holds the
  * last iterate), ODWF_EBREAKDOWN on a breakdown.
  */
