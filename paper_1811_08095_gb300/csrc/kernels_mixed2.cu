@@ -45,22 +45,23 @@ struct RawSite<SpBF16> { uint4 q[3]; float sc; };
 template <>
 struct RawSite<SpF32> { float4 q[6]; float sc; };
 
-// 32-bit chunk index of (h, s): h * nch * ns + s (hop2_supported bounds the field size)
+// 32-bit chunk index of (h, s): h * nch * ns + s (hop2_supported bounds the field size).
+// Threads past the last site load site 0's neighbours (valid addresses) and store nothing.
 template <class SP>
-__device__ __forceinline__ void fetch_site(const void* base, const float* norm, unsigned h, int s, int ns, bool valid,
+__device__ __forceinline__ void fetch_site(const void* base, const float* norm, unsigned h, int s, int ns,
                                            RawSite<SP>& r) {
     if (std::is_same<SP, SpF32>::value) {
         const float4* p = reinterpret_cast<const float4*>(base) + (h * (6u * ns) + (unsigned)s);
         float4* q = reinterpret_cast<float4*>(&r);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) q[k] = valid ? __ldg(p + k * ns) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < 6; ++k) q[k] = __ldg(p + k * ns);
         r.sc = 1.f;
     } else {
         const uint4* p = reinterpret_cast<const uint4*>(base) + (h * (3u * ns) + (unsigned)s);
         uint4* q = reinterpret_cast<uint4*>(&r);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) q[k] = valid ? __ldg(p + k * ns) : make_uint4(0u, 0u, 0u, 0u);
-        r.sc = valid ? __ldg(norm + (h * (unsigned)ns + (unsigned)s)) : 0.f;
+        for (int k = 0; k < 3; ++k) q[k] = __ldg(p + k * ns);
+        r.sc = __ldg(norm + (h * (unsigned)ns + (unsigned)s));
     }
 }
 
@@ -238,11 +239,11 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
     constexpr float SF = DAG ? 1.f : -1.f;
     // neighbour j + 1 is fetched before neighbour j is processed
     RawSite<SP> rs[2];
-    fetch_site<SP>(in, in_n, (unsigned)nb[0], s, NS, valid, rs[0]);
+    fetch_site<SP>(in, in_n, (unsigned)nb[0], s, NS, rs[0]);
 #define ODWF_HOP_DIR(MU_, DIR_)                                                                                   \
     {                                                                                                             \
         constexpr int j_ = 2 * MU_ + DIR_;                                                                        \
-        if (j_ < 7) fetch_site<SP>(in, in_n, (unsigned)nb[j_ + 1 < 8 ? j_ + 1 : 7], s, NS, valid, rs[(j_ + 1) & 1]); \
+        if (j_ < 7) fetch_site<SP>(in, in_n, (unsigned)nb[j_ + 1 < 8 ? j_ + 1 : 7], s, NS, rs[(j_ + 1) & 1]);        \
         const float sgn_ = (flip & (1u << j_)) ? -1.f : 1.f;                                                     \
         const LinkStaged ls_{L4 + j_ * 9};                                                                        \
         hop_dir_packed<SP, MU_, DIR_ == 1>(rs[j_ & 1], sgn_, DIR_ == 0 ? SF : -SF, ls_, AUr, AUi, ADr, ADi, ADSr,  \
@@ -288,6 +289,7 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
             acc[k] += z[k];
             nrm = fmaf(acc[k], acc[k], nrm);
         }
+        if (!valid) nrm = 0.f;  // a site past the end computed site 0's neighbours: no contribution
         minv_apply_f(acc, cf, r, s, NS, true, 1.f);
         if (valid) SpinorIO<SP, float>::store(P.out.d(sys), P.out.n(sys), (size_t)h, s, NS, acc);
     } else if (KIND == K3) {
