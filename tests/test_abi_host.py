@@ -88,3 +88,13 @@ def test_create_rejects_bad_sizes(lib):
         rc = lib.odwf_create(ctypes.byref(lat), ns, 1.3, 0.01, om.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h))
         assert rc == odwf._lib.ODWF_EINVAL, dims
     assert lib.odwf_create(None, 8, 1.3, 0.01, None, ctypes.byref(h)) == odwf._lib.ODWF_EINVAL
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without libodwf.so the binding raises instead of computing anything."""
+    from paper_1811_08095_gb300 import _lib
+
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libodwf.so"))
+    with pytest.raises(RuntimeError, match="no fallback"):
+        _lib.load()
