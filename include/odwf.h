@@ -40,6 +40,10 @@
  * Errors: every entry point returns an int status (ODWF_OK = 0); no exception
  * crosses the ABI.  odwf_last_error() gives a message for the calling thread's
  * last failure.
+ *
+ * Threads: a handle keeps workspaces and solver state, so calls on one handle must not
+ * overlap (use one handle per thread, or serialise); different handles are independent.
+ * The serving functions (serve_*) may be called from any number of threads.
  */
 #ifndef ODWF_H
 #define ODWF_H
