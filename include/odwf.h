@@ -200,7 +200,12 @@ int odwf_apply_m5(odwf_handle* h, void* out, const void* in, long n_sites, int o
  *             loads the library keeps until the process exits.
  *   set-up    the first call on each device looks up that array's device address
  *             (cudaGetSymbolAddress) with the device current; make that first call
- *             before any stream capture begins.
+ *             before any stream capture begins.  Under CUDA's lazy module loading (the
+ *             default) that first call is also when the device reserves the array's 24 MiB:
+ *             a caller whose own pool will take most of the GPU's memory should make one
+ *             small call (n_sites = 1) on each device before reserving its pool.  With
+ *             CUDA_MODULE_LOADING=EAGER the array is reserved when the context is created.
+ *             in and out must be memory of the current device (ODWF_EINVAL otherwise).
  *   sharing   every call uses the same array, which keeps the last call's contents
  *             (each call writes all it reads first); calls whose work overlaps on the
  *             GPU -- different streams, or host threads -- race on it and must be
@@ -233,6 +238,45 @@ int odwf_cg_solve(odwf_handle* h, void* x, const void* b, const odwf_solve_param
 int odwf_cg_solve_batched(odwf_handle* h, int nsys, void* const* x, const void* const* b,
                           const double* mq, const odwf_solve_params* params,
                           odwf_solve_stats* stats, void* stream);
+
+/*
+ * One iteration of the mixed-precision inner CG (Sec. 2's CG on the normal equations, with
+ * the storage formats of odwf_cg_solve's mixed modes), through exactly the kernels the
+ * batched solver launches every iteration, returning every field the iteration stores.  It
+ * is exposed so that each stored field can be checked against an FP64 reference element by
+ * element.  With W the hopping sum of D_w = (4 - m0) - W/2, B = rho + sigma L and
+ * M = (4 - m0) B + 1 - L (so H = -1/2 W B and S = 1 - M^-1 H_eo M^-1 H_oe):
+ *   p     = r + beta p_prev              (stored in `prec`)
+ *   chi_p = B p                          (stored; the non-dagger hops read it)
+ *   chi_t = B M^-1 (-1/2 W chi_p)        (odd sites; = B t with t = M^-1 H_oe p)
+ *   s     = p - M^-1 (-1/2 W chi_t)      (= S p, not stored);  pAp = |s|^2;  alpha = rr / pAp
+ *   a     = M^-dag s
+ *   c     = M^-dag B^dag (-1/2 W^dag a)  (odd sites)
+ *   Ap    = M^dag a - B^dag (-1/2 W^dag c)   (= S^dag S p, not stored)
+ *   r_new = r - alpha Ap,  x_new = x + alpha p   (FP32);  rr_new = |r_new|^2
+ * prec: ODWF_F32, ODWF_F16 or ODWF_BF16 (FP16/BF16 with one FP32 scale per 5D site);
+ * link_recon: 12 or 18 (0 = 12); mq: the mass of this system (r = mq / (2 m0)).
+ * p_prev, r, x: even-site fields (SCHUR_EVEN layout, host or device); r and x are rounded to
+ * FP32 and p_prev to `prec` on entry.  outs: 8 pointers (host or device, each may be NULL),
+ * receiving the stored fields in the SCHUR_EVEN layout of their parity (odd-site fields in
+ * the same [s][lex/2][spin][colour] order over odd sites):
+ *   0 p_prev as stored, 1 p, 2 chi_p, 3 chi_t (odd), 4 a, 5 c (odd), 6 r_new, 7 x_new.
+ * sc: in: beta, rr (> 0); out: pAp, alpha, rr_new, status (ODWF_EBREAKDOWN when pAp <= 0 or
+ * non-finite; the later fields are then not written by the kernels).  Needs Ns = 8 or 16.
+ * Allocates its own workspaces (freed by odwf_destroy); returns when the outputs are written.
+ */
+typedef struct {
+    double beta;    /* in */
+    double rr;      /* in: |r|^2 of the incoming residual */
+    double pAp;     /* out: |S p|^2 */
+    double alpha;   /* out: rr / pAp */
+    double rr_new;  /* out: |r_new|^2 */
+    int32_t status; /* out */
+    int32_t reserved;
+} odwf_cg_step_scalars;
+
+int odwf_mixed_cg_step(odwf_handle* h, int prec, int link_recon, double mq, const void* p_prev, const void* r,
+                       const void* x, void* const* outs, odwf_cg_step_scalars* sc, void* stream);
 
 /* ----------------------------------------------------------------------------------
  * Kernel timing (no counterpart in the paper; used to place the kernels on the roofline).

@@ -52,8 +52,9 @@ def _load():
             lib.oracle_d5.argtypes = [P, P, I, I, D, D, P, P, P, P, I]
             lib.oracle_m5.argtypes = [I, D, D, P, P, ctypes.c_long, P, P, I]
             lib.oracle_m5.restype = I
+            lib.oracle_b5.argtypes = [I, D, D, P, P, ctypes.c_long, P, P, I]
             lib.oracle_schur.argtypes = [P, P, I, I, D, D, P, P, P, P, I]
-            lib.oracle_cg.argtypes = [I, P, P, I, I, D, D, P, P, P, P, D, I, I, ctypes.POINTER(D)]
+            lib.oracle_cg.argtypes = [I, P, P, I, I, D, D, P, P, P, P, D, I, I, ctypes.POINTER(D), P]
             lib.oracle_cg.restype = I
             lib.oracle_num_threads.restype = I
             lib.oracle_gammas.argtypes = [P]
@@ -140,6 +141,32 @@ def m5(psi, m0: float, mq: float, omega=None, op: int = M, rho=None, sigma=None)
     return out
 
 
+def b5(psi, m0: float, mq: float, omega=None, dagger: bool = False, rho=None, sigma=None) -> np.ndarray:
+    """The chiral shift B = rho + sigma L of D = D_w B + 1 - L (or B^dag = rho + L^dag sigma) on
+    any 5D field whose first axis is s and whose last two axes are (spin, colour)."""
+    psi = _c(psi)
+    ns = psi.shape[0]
+    rho, sigma = _rs(ns, omega, rho, sigma)
+    nsite = psi.size // (12 * ns)
+    out = np.empty_like(psi)
+    _load().oracle_b5(ns, float(m0), float(mq), _p(rho), _p(sigma), nsite, _p(psi), _p(out), int(dagger))
+    return out
+
+
+def hop_w(U, half, parity_in: int, m0: float, tbc: bool = True, dagger: bool = False) -> np.ndarray:
+    """-1/2 W psi (or -1/2 W^dag psi) on a half field (Ns, V/2, 4, 3) of parity `parity_in`,
+    returned on the other parity: the hopping part of D_w = (4 - m0) - W/2, taken from the
+    Wilson operator applied slice by slice to the parity-embedded field (its diagonal term
+    stays on the input parity and drops out)."""
+    lt, lz, ly, lx = U.shape[1:5]
+    dims = (lx, ly, lz, lt)
+    full = from_parity(_c(half), dims, parity_in)
+    out = np.empty_like(full)
+    for s in range(full.shape[0]):
+        out[s] = dw(U, full[s], m0, tbc, dagger)
+    return to_parity(out, dims, 1 - parity_in)
+
+
 def schur(U, psi_e, m0: float, mq: float, omega=None, tbc: bool = True, dagger: bool = False,
           rho=None, sigma=None) -> np.ndarray:
     """Even-odd Schur operator S = 1 - M^-1 H_eo M^-1 H_oe (or S^dag) on an even-site field
@@ -158,10 +185,12 @@ SCHUR_NORMAL, FULL_NORMAL = 0, 1
 
 
 def cg(U, b, m0: float, mq: float, omega=None, tbc: bool = True, system: int = SCHUR_NORMAL,
-       tol: float = 1e-12, max_iter: int = 100000, x0=None, rho=None, sigma=None):
+       tol: float = 1e-12, max_iter: int = 100000, x0=None, rho=None, sigma=None, coefs=None):
     """CG on S^dag S x = b (even-site b) or D^dag D x = b (full b).
 
-    Returns (x, iterations, true relative residual); iterations = -1 if not converged."""
+    Returns (x, iterations, true relative residual); iterations = -1 if not converged.
+    coefs: optional float64 array of 2 * max_iter entries that receives alpha_k, beta_k of
+    every iteration (the Lanczos coefficients: see lanczos_extremes)."""
     U = _c(U)
     b = _c(b)
     ns = b.shape[0]
@@ -170,8 +199,25 @@ def cg(U, b, m0: float, mq: float, omega=None, tbc: bool = True, system: int = S
     res = ctypes.c_double(0.0)
     it = _load().oracle_cg(int(system), _p(U), _p(_dims(U)), int(tbc), ns, float(m0), float(mq),
                            _p(rho), _p(sigma), _p(b), _p(x), float(tol), int(max_iter),
-                           int(x0 is not None), ctypes.byref(res))
+                           int(x0 is not None), ctypes.byref(res),
+                           None if coefs is None else _p(coefs))
     return x, int(it), float(res.value)
+
+
+def lanczos_extremes(coefs, iters):
+    """Smallest and largest eigenvalue estimates of the normal operator from `iters` CG
+    iterations' alpha_k, beta_k (CG is the Lanczos process: its tridiagonal matrix has
+    T_kk = 1/alpha_k + beta_{k-1}/alpha_{k-1}, T_{k,k+1} = sqrt(beta_k)/alpha_k, and the extreme
+    eigenvalues of T converge to those of the operator from inside the spectrum)."""
+    a = np.asarray(coefs[0:2 * iters:2], dtype=np.float64)
+    bt = np.asarray(coefs[1:2 * iters:2], dtype=np.float64)
+    n = len(a)
+    diag = 1.0 / a
+    diag[1:] += bt[:-1] / a[:-1]
+    off = np.sqrt(bt[:-1]) / a[:-1]
+    T = np.diag(diag) + np.diag(off, 1) + np.diag(off, -1)
+    ev = np.linalg.eigvalsh(T) if n else np.array([np.nan])
+    return float(ev[0]), float(ev[-1])
 
 
 def normal_op(U, psi, m0, mq, omega=None, tbc=True, system=SCHUR_NORMAL, rho=None, sigma=None):

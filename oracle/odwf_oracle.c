@@ -354,6 +354,41 @@ int oracle_m5(int Ns, double m0, double mq, const double *rho, const double *sig
     return rc;
 }
 
+/*
+ * The chiral shift B = diag(rho) + diag(sigma) L of the operator D = D_w B + 1 - L
+ * (Sec. 2's (rho_s D_w + 1) psi_s + (sigma_s D_w - 1)(L psi)_s, regrouped), on a 5D field of
+ * V sites per s-slice:  dagger = 0:  (B psi)_s = rho_s psi_s + sigma_s (L psi)_s
+ *                       dagger = 1:  B^dag phi = rho phi + L^dag (sigma phi)
+ */
+void oracle_b5(int Ns, double m0, double mq, const double *rho, const double *sigma,
+               long V, const cplx *in, cplx *out, int dagger)
+{
+    cplx *Lm = malloc(sizeof(cplx) * 16 * Ns * Ns);
+    cplx *t = malloc(sizeof(cplx) * 12 * V * Ns);
+    build_L(Ns, mq / (2.0 * m0), Lm);
+    if (!dagger) {
+        apply_L(Lm, Ns, V, in, t, 0);
+        for (int s = 0; s < Ns; ++s)
+            for (long k = 0; k < 12 * V; ++k) {
+                const long o = 12 * (long)s * V + k;
+                out[o] = rho[s] * in[o] + sigma[s] * t[o];
+            }
+    } else {
+        cplx *u = malloc(sizeof(cplx) * 12 * V * Ns);
+        for (int s = 0; s < Ns; ++s)
+            for (long k = 0; k < 12 * V; ++k) u[12 * (long)s * V + k] = sigma[s] * in[12 * (long)s * V + k];
+        apply_L(Lm, Ns, V, u, t, 1);
+        for (int s = 0; s < Ns; ++s)
+            for (long k = 0; k < 12 * V; ++k) {
+                const long o = 12 * (long)s * V + k;
+                out[o] = rho[s] * in[o] + t[o];
+            }
+        free(u);
+    }
+    free(Lm);
+    free(t);
+}
+
 static int parity_of(const int *L, long i)
 {
     const int x = i % L[0], y = (i / L[0]) % L[1], z = (i / ((long)L[0] * L[1])) % L[2],
@@ -450,8 +485,11 @@ static void normal_op(int system, const cplx *U, const int *L, int tbc, int Ns, 
  */
 int oracle_cg(int system, const cplx *U, const int *L, int tbc, int Ns, double m0, double mq,
               const double *rho, const double *sigma, const cplx *b, cplx *x, double tol,
-              int max_iter, int x_is_guess, double *res_out)
+              int max_iter, int x_is_guess, double *res_out, double *coef_out)
 {
+    /* coef_out (may be NULL): 2 * max_iter doubles; iteration k writes its alpha_k and
+     * beta_k to coef_out[2k], coef_out[2k+1] (the Lanczos coefficients of the Krylov
+     * space, from which the extreme eigenvalues of the normal operator follow). */
     const long V = (long)L[0] * L[1] * L[2] * L[3];
     const long n = 12 * Ns * (system == 0 ? V / 2 : V);
     cplx *r = malloc(sizeof(cplx) * n), *p = malloc(sizeof(cplx) * n);
@@ -471,6 +509,7 @@ int oracle_cg(int system, const cplx *U, const int *L, int tbc, int Ns, double m
         const double rr_new = dot_re(r, r, n);
         const double beta = rr_new / rr;
         for (long k = 0; k < n; ++k) p[k] = r[k] + beta * p[k];
+        if (coef_out) { coef_out[2 * it] = alpha; coef_out[2 * it + 1] = beta; }
         rr = rr_new;
         ++it;
     }

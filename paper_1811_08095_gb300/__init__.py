@@ -132,6 +132,21 @@ class Handle:
         check(self._lib.odwf_apply_m5(self._h, ptr(out), ptr(inp), int(n_sites), int(op), stream_ptr(stream)))
         return out
 
+    def mixed_cg_step(self, p_prev, r, x, outs, beta, rr, prec="f16", link_recon=12, mq=None, stream=None):
+        """odwf_mixed_cg_step: one production mixed CG iteration; `outs` is a list of 8 fields
+        (or None) receiving p_prev as stored, p, chi_p, chi_t, a, c, r_new, x_new.  Returns the
+        scalars as a dict."""
+        assert len(outs) == 8
+        oa = (ctypes.c_void_p * 8)(*[(ptr(o).value if o is not None else None) for o in outs])
+        sc = _lib.odwf_cg_step_scalars()
+        sc.beta = float(beta)
+        sc.rr = float(rr)
+        pr = PREC[prec] if isinstance(prec, str) else int(prec)
+        check(self._lib.odwf_mixed_cg_step(self._h, pr, int(link_recon), self.mq if mq is None else float(mq),
+                                           ptr(p_prev), ptr(r), ptr(x), ctypes.cast(oa, ctypes.c_void_p),
+                                           ctypes.byref(sc), stream_ptr(stream)))
+        return {"pAp": sc.pAp, "alpha": sc.alpha, "rr_new": sc.rr_new, "status": sc.status}
+
     def cg_solve(self, x, b, tol=1e-10, max_iter=100000, prec="f64", delta=0.01, system=ODWF_SYS_SCHUR_NORMAL,
                  link_recon=12, mq=None, check_every=8, stream=None, raise_on_error=True):
         p = _params(tol, max_iter, prec, delta, system, link_recon, mq, check_every)

@@ -60,6 +60,12 @@ class odwf_kernel_prof(ctypes.Structure):
                 ("bytes_per_launch", ctypes.c_double)]
 
 
+class odwf_cg_step_scalars(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("rr", ctypes.c_double), ("pAp", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("rr_new", ctypes.c_double), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class OdwfError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("%s (%d): %s" % (STATUS_NAMES.get(code, "?"), code, msg))
@@ -86,6 +92,7 @@ _SIGS = {
     "odwf_apply_normal_prec": ([P, P, P, I, I, P], I),
     "odwf_apply_m5": ([P, P, P, ctypes.c_long, I, P], I),
     "odwf_apply_m5_noalloc": ([I, D, D, P, P, P, ctypes.c_long, I, P], I),
+    "odwf_mixed_cg_step": ([P, I, I, D, P, P, P, P, ctypes.POINTER(odwf_cg_step_scalars), P], I),
     "odwf_cg_solve": ([P, P, P, ctypes.POINTER(odwf_solve_params), P, P], I),
     "odwf_cg_solve_batched": ([P, I, P, P, P, ctypes.POINTER(odwf_solve_params), P, P], I),
     "odwf_profile_enable": ([I], I),

@@ -311,37 +311,9 @@ int BatchCG::launch_iterations(int k, int lo, int n, cudaStream_t s) {
                 ODWF_CK(e_);
             }
         } else if (v2) {
-            auto P = params<float>(1);
-            P.gate = 1;
-            P.need_status = kRunning;
-            P.sys_base = lo;
-            const FieldRef ins[4] = {Chil.ref(), Tl.ref(), Al.ref(), Cl.ref()};
-            const FieldRef outs[4] = {Tl.ref(), Al.ref(), Cl.ref(), FieldRef{}};
-            const FieldRef zs[4] = {FieldRef{}, Pl.ref(), FieldRef{}, Al.ref()};
-            for (int k = 0; k < 4; ++k) {
-                P.p_out = (k & 1) ? 0 : 1;
-                P.in = ins[k];
-                P.out = outs[k];
-                P.z = zs[k];
-                if (k == 3) {
-                    P.cg_r = Rin.ref();
-                    P.cg_x = Xin.ref();
-                    P.cg_p = Pl.ref();
-                }
-                auto pb_ = prof_begin(pcls[k], s);
-                P.prof_count = pb_.dev_count;
-                const cudaError_t e_ = launch_hop2(P, k + 1, low, lk, n, s);
-                prof_end(pb_, s);
-                P.prof_count = nullptr;
-                ODWF_CK(e_);
-            }
-            {
-                auto pb_ = prof_begin(pcls[4], s);
-                const cudaError_t e_ = launch_p_update2(low, E->ns, Rin.ref(), Pl.ref(), Chil.ref(), E->vh(), 1, E->cf32,
-                                                        r_dev, st, 1, kRunning, lo, n, pb_.dev_count, s);
-                prof_end(pb_, s);
-                ODWF_CK(e_);
-            }
+            int rc = launch_v2_hops(lo, n, s);
+            if (!rc) rc = launch_v2_pupdate(1, lo, n, 1, kRunning, s);
+            if (rc) return rc;
         } else {
             auto P = params<float>(1);
             P.gate = 1;
@@ -379,6 +351,58 @@ int BatchCG::launch_iterations(int k, int lo, int n, cudaStream_t s) {
             }
         }
     }
+    return ODWF_OK;
+}
+
+// The four hops K1..K4 of one second-generation mixed iteration over slots lo..lo+n-1 (the
+// non-dagger hops read chi = B psi): the launches the solver replays every iteration.
+int BatchCG::launch_v2_hops(int lo, int n, cudaStream_t s) {
+    auto P = params<float>(1);
+    P.gate = 1;
+    P.need_status = kRunning;
+    P.sys_base = lo;
+    const FieldRef ins[4] = {Chil.ref(), Tl.ref(), Al.ref(), Cl.ref()};
+    const FieldRef outs[4] = {Tl.ref(), Al.ref(), Cl.ref(), FieldRef{}};
+    const FieldRef zs[4] = {FieldRef{}, Pl.ref(), FieldRef{}, Al.ref()};
+    for (int k = 0; k < 4; ++k) {
+        P.p_out = (k & 1) ? 0 : 1;
+        P.in = ins[k];
+        P.out = outs[k];
+        P.z = zs[k];
+        if (k == 3) {
+            P.cg_r = Rin.ref();
+            P.cg_x = Xin.ref();
+            P.cg_p = Pl.ref();
+        }
+        auto pb_ = prof_begin(pcls[k], s);
+        P.prof_count = pb_.dev_count;
+        const cudaError_t e_ = launch_hop2(P, k + 1, low, lk, n, s);
+        prof_end(pb_, s);
+        P.prof_count = nullptr;
+        ODWF_CK(e_);
+    }
+    return ODWF_OK;
+}
+
+// p = r + beta p (mode 1) or p = r (mode 0), chi_p = B p, for the slots whose status is `need`.
+int BatchCG::launch_v2_pupdate(int mode, int lo, int n, int gate, int need, cudaStream_t s) {
+    auto pb_ = prof_begin(pcls[4], s);
+    const cudaError_t e_ = launch_p_update2(low, E->ns, Rin.ref(), Pl.ref(), Chil.ref(), E->vh(), mode, E->cf32, r_dev,
+                                            st, gate, need, lo, n, pb_.dev_count, s);
+    prof_end(pb_, s);
+    ODWF_CK(e_);
+    return ODWF_OK;
+}
+
+int BatchCG::set_state(int slot, const SysState& init, double r, cudaStream_t s) {
+    if (slot < 0 || slot >= cap) return fail(ODWF_EINVAL, "set_state: bad slot");
+    double* rpin = reinterpret_cast<double*>(st_host + 2 * cap) + slot;
+    *rpin = r;
+    ODWF_CK(cudaMemcpyAsync(r_dev + slot, rpin, sizeof(double), cudaMemcpyHostToDevice, s));
+    SysState* stage = st_host + cap + slot;
+    *stage = init;
+    ODWF_CK(cudaMemcpyAsync(st + slot, stage, sizeof(SysState), cudaMemcpyHostToDevice, s));
+    ODWF_CK(cudaStreamSynchronize(s));
     return ODWF_OK;
 }
 

@@ -95,6 +95,11 @@ struct BatchCG {
     int poll(cudaStream_t s);                      // refresh st_host (synchronizes s)
     int service(cudaStream_t s);                   // reliable updates for parked slots
     int finalize(int slot, double2* x_ext, cudaStream_t s, double* true_resid);
+    // second-generation mixed iteration pieces (v2 only): K1..K4 hops, and the p update
+    int launch_v2_hops(int lo, int n, cudaStream_t s);
+    int launch_v2_pupdate(int mode, int lo, int n, int gate, int need, cudaStream_t s);
+    // write a slot's scalars (and r = m_q / (2 m0)) directly; synchronizes s
+    int set_state(int slot, const SysState& init, double r, cudaStream_t s);
     bool slot_running(int i) const;
     bool slot_finished(int i) const;
     int any_running() const;

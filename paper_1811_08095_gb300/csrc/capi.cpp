@@ -1,6 +1,8 @@
 // extern "C" entry points declared in include/odwf.h.
 #include <cmath>
+#include <initializer_list>
 #include <new>
+#include <string>
 
 #include "engine.h"
 
@@ -20,6 +22,30 @@ using odwf::fail;
     catch (...) {                                                   \
         return fail(ODWF_EINVAL, "unexpected exception");           \
     }
+
+namespace {
+// A handle's kernels run on the current device and use memory of the device it was created
+// on: both must agree, and every device pointer argument must belong to that device.
+int on_handle_device(odwf_handle* h, const char* fn, std::initializer_list<const void*> ptrs) {
+    int dev = -1;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return odwf::cuda_fail(e, "cudaGetDevice");
+    if (dev != h->e.device)
+        return fail(ODWF_EINVAL, std::string(fn) + ": the handle belongs to GPU " + std::to_string(h->e.device) +
+                                     ", but GPU " + std::to_string(dev) + " is current");
+    for (const void* p : ptrs) {
+        const int rc = odwf::check_ptr_device(p, dev, fn);
+        if (rc) return rc;
+    }
+    return ODWF_OK;
+}
+}  // namespace
+
+#define ON_DEVICE(h, fn, ...)                                   \
+    do {                                                        \
+        const int rc_ = on_handle_device(h, fn, {__VA_ARGS__}); \
+        if (rc_) return rc_;                                    \
+    } while (0)
 
 extern "C" {
 
@@ -59,6 +85,7 @@ int odwf_destroy(odwf_handle* h) {
 int odwf_set_gauge(odwf_handle* h, const void* U, void* stream) {
     GUARD_BEGIN
     if (!h) return fail(ODWF_EINVAL, "odwf_set_gauge: null handle");
+    ON_DEVICE(h, "odwf_set_gauge", U);
     return h->e.set_gauge(U, (cudaStream_t)stream);
     GUARD_END
 }
@@ -66,6 +93,7 @@ int odwf_set_gauge(odwf_handle* h, const void* U, void* stream) {
 int odwf_apply(odwf_handle* h, void* out, const void* in, int mode, void* stream) {
     GUARD_BEGIN
     if (!h) return fail(ODWF_EINVAL, "odwf_apply: null handle");
+    ON_DEVICE(h, "odwf_apply", out, in);
     return h->e.apply(out, in, mode, false, (cudaStream_t)stream);
     GUARD_END
 }
@@ -73,6 +101,7 @@ int odwf_apply(odwf_handle* h, void* out, const void* in, int mode, void* stream
 int odwf_apply_dagger(odwf_handle* h, void* out, const void* in, int mode, void* stream) {
     GUARD_BEGIN
     if (!h) return fail(ODWF_EINVAL, "odwf_apply_dagger: null handle");
+    ON_DEVICE(h, "odwf_apply_dagger", out, in);
     return h->e.apply(out, in, mode, true, (cudaStream_t)stream);
     GUARD_END
 }
@@ -80,6 +109,7 @@ int odwf_apply_dagger(odwf_handle* h, void* out, const void* in, int mode, void*
 int odwf_apply_normal(odwf_handle* h, void* out, const void* in, int system, void* stream) {
     GUARD_BEGIN
     if (!h) return fail(ODWF_EINVAL, "odwf_apply_normal: null handle");
+    ON_DEVICE(h, "odwf_apply_normal", out, in);
     return h->e.apply_normal(out, in, system, (cudaStream_t)stream);
     GUARD_END
 }
@@ -87,6 +117,7 @@ int odwf_apply_normal(odwf_handle* h, void* out, const void* in, int system, voi
 int odwf_apply_normal_prec(odwf_handle* h, void* out, const void* in, int prec, int link_recon, void* stream) {
     GUARD_BEGIN
     if (!h) return fail(ODWF_EINVAL, "odwf_apply_normal_prec: null handle");
+    ON_DEVICE(h, "odwf_apply_normal_prec", out, in);
     return h->e.apply_low_normal(out, in, prec, link_recon, (cudaStream_t)stream);
     GUARD_END
 }
@@ -94,7 +125,19 @@ int odwf_apply_normal_prec(odwf_handle* h, void* out, const void* in, int prec, 
 int odwf_apply_m5(odwf_handle* h, void* out, const void* in, long n_sites, int op, void* stream) {
     GUARD_BEGIN
     if (!h) return fail(ODWF_EINVAL, "odwf_apply_m5: null handle");
+    ON_DEVICE(h, "odwf_apply_m5", out, in);
     return h->e.apply_m5(out, in, n_sites, op, (cudaStream_t)stream);
+    GUARD_END
+}
+
+int odwf_mixed_cg_step(odwf_handle* h, int prec, int link_recon, double mq, const void* p_prev, const void* r,
+                       const void* x, void* const* outs, odwf_cg_step_scalars* sc, void* stream) {
+    GUARD_BEGIN
+    if (!h) return fail(ODWF_EINVAL, "odwf_mixed_cg_step: null handle");
+    ON_DEVICE(h, "odwf_mixed_cg_step", p_prev, r, x);
+    if (outs)
+        for (int i = 0; i < 8; ++i) ON_DEVICE(h, "odwf_mixed_cg_step", outs[i]);
+    return h->e.mixed_cg_step(prec, link_recon, mq, p_prev, r, x, outs, sc, (cudaStream_t)stream);
     GUARD_END
 }
 
@@ -102,6 +145,7 @@ int odwf_cg_solve(odwf_handle* h, void* x, const void* b, const odwf_solve_param
                   void* stream) {
     GUARD_BEGIN
     if (!h) return fail(ODWF_EINVAL, "odwf_cg_solve: null handle");
+    ON_DEVICE(h, "odwf_cg_solve", x, b);
     void* xs[1] = {x};
     const void* bs[1] = {b};
     return h->e.solve(1, xs, bs, nullptr, params, stats, (cudaStream_t)stream);
@@ -112,6 +156,8 @@ int odwf_cg_solve_batched(odwf_handle* h, int nsys, void* const* x, const void* 
                           const odwf_solve_params* params, odwf_solve_stats* stats, void* stream) {
     GUARD_BEGIN
     if (!h) return fail(ODWF_EINVAL, "odwf_cg_solve_batched: null handle");
+    if (x && b && nsys > 0)
+        for (int i = 0; i < nsys; ++i) ON_DEVICE(h, "odwf_cg_solve_batched", x[i], b[i]);
     if (params && params->system != ODWF_SYS_SCHUR_NORMAL)
         return fail(ODWF_EINVAL, "odwf_cg_solve_batched: SCHUR_NORMAL only");
     return h->e.solve(nsys, x, b, mq, params, stats, (cudaStream_t)stream);

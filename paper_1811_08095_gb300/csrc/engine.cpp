@@ -31,6 +31,19 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+int check_ptr_device(const void* p, int dev, const char* what) {
+    if (!p) return ODWF_OK;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return ODWF_OK;  // not known to CUDA: host memory
+    }
+    if (a.type == cudaMemoryTypeDevice && a.device != dev)
+        return fail(ODWF_EINVAL, std::string(what) + ": pointer is device memory of GPU " + std::to_string(a.device) +
+                                     ", but the call runs on GPU " + std::to_string(dev));
+    return ODWF_OK;
+}
+
 Engine::~Engine() {
     for (auto& kv : ws)
         if (kv.second.p) cudaFree(kv.second.p);

@@ -24,6 +24,9 @@ int cuda_fail(cudaError_t e, const char* what);
     } while (0)
 
 bool is_device_ptr(const void* p);
+// ODWF_EINVAL when p is device memory of a GPU other than `dev` (kernels on `dev` cannot read it
+// without peer access); host, managed and unknown pointers pass.
+int check_ptr_device(const void* p, int dev, const char* what);
 
 // A device buffer owned by the engine.
 struct DevBuf {
@@ -98,6 +101,8 @@ struct Engine {
     int apply_normal(void* out, const void* in, int system, cudaStream_t st);
     int apply_m5(void* out, const void* in, long n_sites, int op, cudaStream_t st);
     int apply_low_normal(void* out, const void* in, int prec, int recon, cudaStream_t st);
+    int mixed_cg_step(int prec, int recon, double mq_step, const void* p_prev, const void* r, const void* x,
+                      void* const* outs, odwf_cg_step_scalars* sc, cudaStream_t st);
     int solve(int nsys, void* const* x, const void* const* b, const double* mq_arr, const odwf_solve_params* prm,
               odwf_solve_stats* stats, cudaStream_t st);
     int solve_on(int nsys, void* const* x, const void* const* b, const double* mq_arr,

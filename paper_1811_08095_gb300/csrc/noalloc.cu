@@ -14,7 +14,10 @@
 // every GPU which loads the library keeps until the process exits.  Host code reaches
 // it only through the address that cudaGetSymbolAddress returns for the current device
 // (the array's name in host code is a host-side stand-in, not a device address); that
-// look-up happens on the first call on each device, with the device current.
+// look-up happens on the first call on each device, with the device current.  Under CUDA's
+// lazy module loading (the default) the array is reserved when this file's module is first
+// used on a device -- that same first call -- not when the library is loaded; with
+// CUDA_MODULE_LOADING=EAGER it is reserved when the device's context is created.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -28,6 +31,7 @@ namespace odwf {
 
 int fail(int code, const std::string& msg);
 bool is_device_ptr(const void* p);
+int check_ptr_device(const void* p, int dev, const char* what);
 
 namespace {
 
@@ -76,13 +80,22 @@ extern "C" int odwf_apply_m5_noalloc(int Ns, double m0, double mq, const double*
     if (Ns < 2 || Ns > kMaxNs || (Ns & (Ns - 1)))
         return fail(ODWF_EINVAL, "odwf_apply_m5_noalloc: Ns must be 2, 4, 8, 16 or 32");
     if (op < 0 || op > 3) return fail(ODWF_EINVAL, "odwf_apply_m5_noalloc: op must be 0..3");
-    if (n_sites <= 0 || (size_t)n_sites * (size_t)Ns > kNoAllocMaxSites5)
+    if (n_sites <= 0 || n_sites > (long)(kNoAllocMaxSites5 / (size_t)Ns))
         return fail(ODWF_EINVAL, "odwf_apply_m5_noalloc: n_sites x Ns must be between 1 and 65536 "
                                  "(the size of the library's fixed scratch array)");
     if (!(m0 != 0.0) || !std::isfinite(m0) || !std::isfinite(mq))
         return fail(ODWF_EINVAL, "odwf_apply_m5_noalloc: bad m0 or mq");
     if (!is_device_ptr(in) || !is_device_ptr(out))
         return fail(ODWF_EINVAL, "odwf_apply_m5_noalloc: in and out must be device memory");
+    {
+        int dev = 0;
+        const cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess)
+            return fail(ODWF_ECUDA, std::string("odwf_apply_m5_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+        int rc0 = check_ptr_device(in, dev, "odwf_apply_m5_noalloc (in)");
+        if (!rc0) rc0 = check_ptr_device(out, dev, "odwf_apply_m5_noalloc (out)");
+        if (rc0) return rc0;
+    }
     // coefficients of M = (4 - m0) B + 1 - L, B = rho + sigma L, rho = sigma = omega (kernel parameters)
     Coef5<double> cf;
     std::memset(&cf, 0, sizeof(cf));

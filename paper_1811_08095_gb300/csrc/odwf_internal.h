@@ -135,8 +135,8 @@ struct HalfIO {
                 H2 hv;
                 *reinterpret_cast<uint32_t*>(&hv) = w[j];
                 const float2 f = Half2Cvt<H2>::to_f2(hv);
-                v[8 * k + 2 * j] = (R)(f.x * sc);
-                v[8 * k + 2 * j + 1] = (R)(f.y * sc);
+                v[8 * k + 2 * j] = (R)f.x * (R)sc;  // exact for R = double (the unpacked stored value)
+                v[8 * k + 2 * j + 1] = (R)f.y * (R)sc;
             }
         }
     }

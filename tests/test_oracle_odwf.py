@@ -171,3 +171,71 @@ def test_even_odd_full_solve_reconstruction(oracle_lib, small):
     xo = oracle.m5(eo - hoe, M0, mq, w, oracle.MINV)
     assert np.abs(xe - oracle.to_parity(x, dims, 0)).max() < 1e-11
     assert np.abs(xo - oracle.to_parity(x, dims, 1)).max() < 1e-11
+
+
+def test_lanczos_extremes_match_dense_eigenvalues(oracle_lib, small):
+    """The CG coefficients recorded by oracle.cg give, through the Lanczos tridiagonal matrix,
+    the extreme eigenvalues of S^dag S: checked against a dense eigendecomposition on 2^4 x 4
+    (with enough iterations the Ritz values converge to the ends of the spectrum)."""
+    dims, U = small
+    ns = 4
+    w, _ = zolotarev.omega(ns, 0.05, 6.0, True)
+    mq = 0.05
+    S = dense.dense_schur(U, ns, M0, mq, w)
+    A = S.conj().T @ S
+    ev = np.linalg.eigvalsh(0.5 * (A + A.conj().T))
+    b = syn.gaussian_spinor_even(ns, dims, 23)
+    coefs = np.zeros(2 * 4000)
+    x, it, res = oracle.cg(U, b, M0, mq, w, tol=1e-13, max_iter=4000, coefs=coefs)
+    assert it > 0
+    lmin, lmax = oracle.lanczos_extremes(coefs, it)
+    assert abs(lmax - ev.max()) <= 1e-6 * ev.max()
+    assert abs(lmin - ev.min()) <= 1e-3 * ev.min()
+    # a truncated run sees the spectrum from inside
+    lmin5, lmax5 = oracle.lanczos_extremes(coefs, 5)
+    assert ev.min() * (1 - 1e-9) <= lmin5 and lmax5 <= ev.max() * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("ns", [4, 8])
+def test_b5_is_the_chiral_shift_of_d5(oracle_lib, small, ns):
+    """oracle.b5 against three independent routes (generic rho != sigma, both masses):
+    (1) with U = 0 the Wilson operator is the constant 4 - m0, so D(m0 = 3) - D(m0 = 4) at the
+        same r = m_q/(2 m0) is exactly B (D = D_w B + 1 - L);
+    (2) B^dag is the adjoint of B: <phi, B psi> = <B^dag phi, psi>;
+    (3) the site-local M = (4 - m0) B + 1 - L built densely by oracle.m5, with L = (B - rho)/sigma."""
+    dims, _ = small
+    rho = np.linspace(0.4, 1.9, ns)
+    sig = np.linspace(1.2, 0.3, ns)
+    U0 = np.zeros((4, 2, 2, 2, 2, 3, 3), dtype=np.complex128)
+    psi = syn.gaussian_spinor(ns, dims, 40)
+    phi = syn.gaussian_spinor(ns, dims, 41)
+    for r in (0.02, 0.4):
+        d3 = oracle.d5(U0, psi, 3.0, 2 * 3.0 * r, tbc=False, rho=rho, sigma=sig)
+        d4 = oracle.d5(U0, psi, 4.0, 2 * 4.0 * r, tbc=False, rho=rho, sigma=sig)
+        b = oracle.b5(psi, M0, 2 * M0 * r, rho=rho, sigma=sig)
+        assert np.abs(b - (d3 - d4)).max() < 1e-13
+        bd = oracle.b5(phi, M0, 2 * M0 * r, dagger=True, rho=rho, sigma=sig)
+        lhs = np.vdot(phi.reshape(-1), b.reshape(-1))
+        rhs = np.vdot(bd.reshape(-1), psi.reshape(-1))
+        assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+        m = oracle.m5(psi, M0, 2 * M0 * r, rho=rho, sigma=sig, op=oracle.M)
+        lpsi = (b - rho[:, None, None, None, None, None, None] * psi) / sig[:, None, None, None, None, None, None]
+        assert np.abs(m - ((4 - M0) * b + psi - lpsi)).max() < 1e-13
+
+
+@pytest.mark.parametrize("tbc", [True, False])
+def test_hop_w_composes_to_the_parity_blocks_of_d5(oracle_lib, tbc):
+    """-1/2 W B is the parity-coupling part H of D (D = D_w B + 1 - L, D_w = 4 - m0 - W/2):
+    hop_w(b5(psi_e)) is the odd part of D applied to the even-embedded psi, and
+    b5^dag(hop_w^dag(phi_o)) the even part of D^dag applied to the odd-embedded phi."""
+    dims, ns, mq = (4, 2, 2, 4), 4, 0.3
+    U = syn.gauge_field(dims, 0.5, 3)
+    w = np.linspace(0.3, 1.7, ns)
+    pe = syn.gaussian_spinor_even(ns, dims, 42)
+    po = syn.gaussian_spinor_even(ns, dims, 43)  # any half field, used as odd
+    got = oracle.hop_w(U, oracle.b5(pe, M0, mq, w), 0, M0, tbc)
+    ref = oracle.to_parity(oracle.d5(U, oracle.from_parity(pe, dims, 0), M0, mq, w, tbc), dims, 1)
+    assert np.abs(got - ref).max() < 1e-13
+    got = oracle.b5(oracle.hop_w(U, po, 1, M0, tbc, dagger=True), M0, mq, w, dagger=True)
+    ref = oracle.to_parity(oracle.d5(U, oracle.from_parity(po, dims, 1), M0, mq, w, tbc, dagger=True), dims, 0)
+    assert np.abs(got - ref).max() < 1e-13
