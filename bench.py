@@ -187,6 +187,64 @@ def read_profile(lib):
     return out
 
 
+DSLASH_DIMS = (32, 32, 32, 32)
+DSLASH_TRAFFIC = os.path.join(ROOT, "profiles", "ncu_traffic_dslash.txt")
+
+
+def dslash_roofline(args, dev, reps=20):
+    """Standalone hop kernels on 32^4 x 16 (odwf_time_kernel: one warm-up launch, then `reps`
+    launches between two CUDA events on the launching stream).  Per kernel: average launch time,
+    algorithmic bytes per launch (each field once per system plus the links once), GB/s and the
+    fraction of the measured HBM peak; ncu DRAM traffic where profiles/ holds a capture."""
+    import torch
+
+    import odwf_synth as syn
+    import paper_1811_08095_gb300 as odwf
+
+    peak, peak_kind = measured_peaks()
+    dims = DSLASH_DIMS
+    vh = dims[0] * dims[1] * dims[2] * dims[3] // 2
+    w, _ = odwf.odwf_zolotarev_omega(NS, LRANGE[0], LRANGE[1])
+    U = syn.gauge_field_torch(dims, EPS, 3, device=dev)
+    h = odwf.Handle(dims, NS, M0, MASSES[1], w)
+    h.set_gauge(U)
+    del U
+    g = torch.Generator(device=dev)
+    g.manual_seed(1)
+    fill = torch.randn((NS, vh, 4, 3), dtype=torch.complex128, device=dev, generator=g)
+    traffic = {}
+    if os.path.exists(DSLASH_TRAFFIC):
+        for line in open(DSLASH_TRAFFIC):
+            parts = line.split()
+            if len(parts) >= 3 and not line.startswith("#"):
+                traffic[(parts[0], int(parts[1]))] = float(parts[2])
+    out = {"lattice": "32^4", "Ns": NS, "spinors": "f16 (per-site FP32 scale)", "reps": reps,
+           "timing": "CUDA events around %d launches on the launching stream, after one warm-up launch" % reps,
+           "peak": peak, "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)", "kernels": []}
+    for link_prec in ("f32", "f16"):
+        for nsys in (1, 3):
+            for kind in (1, 2, 3, 4):
+                if link_prec == "f16" and kind != 1:
+                    continue
+                r = h.time_kernel(kind, fill, prec="f16", link_prec=link_prec, nsys=nsys, reps=reps)
+                per_launch = nsys * r["bytes_per_system"] + r["bytes_per_launch"]
+                avg_s = r["total_ms"] / r["launches"] / 1e3
+                gbs = per_launch / avg_s / 1e9
+                tr = traffic.get((r["name"], nsys))
+                out["kernels"].append({"kernel": r["name"], "links": link_prec, "systems": nsys,
+                                       "avg_us": round(avg_s * 1e6, 1), "algorithmic_bytes": per_launch,
+                                       "gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                                       "traffic": tr})
+    h.close()
+    del fill
+    torch.cuda.empty_cache()
+    k1 = [k for k in out["kernels"] if k["kernel"].endswith("K1_chi_minv")]
+    best = max(k1, key=lambda k: k["frac"])
+    out["dslash_k1_best"] = {"kernel": best["kernel"], "links": best["links"], "systems": best["systems"],
+                             "gbs": best["gbs"], "frac": best["frac"]}
+    return out
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -341,6 +399,11 @@ def run_ours(args, world, rank, local):
                 "true_resid": [s["true_resid"] for s in st64],
                 "speedup_mixed_vs_fp64": round(value / world / (len(MASSES) / t64), 2)}
 
+    # ---- the Dslash proper on a working set far larger than L2: the K1 hop
+    # (chi_t = B M^-1 (-1/2 W chi_p)) and the other three hops of the iteration, alone, on
+    # 32^4 x 16 with FP16 spinors (436 MB per field and system), one and three systems
+    dslash = None if args.skip_dslash else dslash_roofline(args, dev)
+
     cpu = None
     if rank == 0 and not args.skip_cpu:
         counts = oracle_iteration_counts()
@@ -376,7 +439,7 @@ def run_ours(args, world, rank, local):
                        "reliable_updates": [s["n_reliable"] for s in all_stats[-1]],
                        "true_resid": [s["true_resid"] for s in all_stats[-1]],
                        "wall_s_timed_region": round(wall_s, 3)},
-            "roofline": roof, "kernels": hops, "fp64_cg": fp64, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "kernels": hops, "dslash": dslash, "fp64_cg": fp64, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -709,6 +772,7 @@ def main():
     ap.add_argument("--drain", type=float, default=60.0, help="serve: extra seconds to finish pending requests")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-dslash", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":

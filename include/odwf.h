@@ -64,7 +64,9 @@ enum {
     ODWF_ETIMEOUT = 5,    /* a bounded wait ran out */
     ODWF_ECUDA = 6,       /* a CUDA runtime call failed */
     ODWF_PENDING = 7,     /* serving: request still queued or running */
-    ODWF_ENOTFOUND = 8    /* serving: unknown ticket or field id */
+    ODWF_ENOTFOUND = 8,   /* serving: unknown ticket or field id */
+    ODWF_ECANCELED = 9,   /* serving: the request was cancelled (serve_cancel) */
+    ODWF_EBUSY = 10       /* serving: the queue is full (serve_set_policy); the request was not taken */
 };
 
 typedef enum { ODWF_F64 = 0, ODWF_F32 = 1, ODWF_F16 = 2, ODWF_BF16 = 3 } odwf_prec;
@@ -98,7 +100,9 @@ typedef struct {
     int32_t link_recon; /* mixed inner links: 12 (two rows, third reconstructed) or 18; 0 = 12 */
     double mq;          /* quark mass for this solve; NaN keeps the handle's m_q */
     int32_t check_every;/* host status poll interval in iterations (0 = 8) */
-    int32_t reserved;
+    int32_t link_prec;  /* mixed inner links: 0 or ODWF_F32 = FP32; ODWF_F16 = FP16 with 12 reals
+                           (24 bytes per link, no scale: SU(3) entries have modulus <= 1; needs
+                           Ns = 8 or 16 and link_recon 0 or 12) */
 } odwf_solve_params;
 
 typedef struct {
@@ -255,7 +259,8 @@ int odwf_cg_solve_batched(odwf_handle* h, int nsys, void* const* x, const void* 
  *   Ap    = M^dag a - B^dag (-1/2 W^dag c)   (= S^dag S p, not stored)
  *   r_new = r - alpha Ap,  x_new = x + alpha p   (FP32);  rr_new = |r_new|^2
  * prec: ODWF_F32, ODWF_F16 or ODWF_BF16 (FP16/BF16 with one FP32 scale per 5D site);
- * link_recon: 12 or 18 (0 = 12); mq: the mass of this system (r = mq / (2 m0)).
+ * link_recon: 12 or 18 (0 = 12); link_prec: as odwf_solve_params.link_prec (ODWF_F16 needs
+ * link_recon 12); mq: the mass of this system (r = mq / (2 m0)).
  * p_prev, r, x: even-site fields (SCHUR_EVEN layout, host or device); r and x are rounded to
  * FP32 and p_prev to `prec` on entry.  outs: 8 pointers (host or device, each may be NULL),
  * receiving the stored fields in the SCHUR_EVEN layout of their parity (odd-site fields in
@@ -275,8 +280,8 @@ typedef struct {
     int32_t reserved;
 } odwf_cg_step_scalars;
 
-int odwf_mixed_cg_step(odwf_handle* h, int prec, int link_recon, double mq, const void* p_prev, const void* r,
-                       const void* x, void* const* outs, odwf_cg_step_scalars* sc, void* stream);
+int odwf_mixed_cg_step(odwf_handle* h, int prec, int link_recon, int link_prec, double mq, const void* p_prev,
+                       const void* r, const void* x, void* const* outs, odwf_cg_step_scalars* sc, void* stream);
 
 /* ----------------------------------------------------------------------------------
  * Kernel timing (no counterpart in the paper; used to place the kernels on the roofline).
@@ -298,6 +303,20 @@ int odwf_profile_enable(int on);
 /* Synchronize the device and copy up to max_entries kernel classes with launches into
  * out; *n_out receives the count. */
 int odwf_profile_read(odwf_kernel_prof* out, int max_entries, int* n_out);
+
+/*
+ * Time one kernel of the production mixed-precision iteration on its own: kind 1..4 = the
+ * hops K1..K4 (see odwf_mixed_cg_step; K1 is the plain Dslash chi_t = B M^-1 (-1/2 W chi_p)),
+ * 5 = the p update.  nsys systems (1..64) share the handle's links; every input field of every
+ * system is filled from `fill` (an even-site field, host or device; any finite values) and
+ * every system runs.  After one warm-up launch, `reps` launches are timed with two CUDA events
+ * on `stream`; out receives the kernel class name, the launch counts, the total time and the
+ * algorithmic bytes (each field read or written once per system, links once per launch).
+ * Results are meaningful as bandwidth when one system's fields exceed the L2 cache.
+ * Allocates its workspaces on the handle (freed by odwf_destroy).
+ */
+int odwf_time_kernel(odwf_handle* h, int kind, int prec, int link_recon, int link_prec, int nsys, int reps,
+                     const void* fill, odwf_kernel_prof* out, void* stream);
 
 /* Number of kernel launches the library has issued in this process (all kernels). */
 long long odwf_launch_count(void);
@@ -350,7 +369,28 @@ int serve_submit(serve_handle* s, const odwf_request* req, uint64_t* ticket);
  */
 int serve_poll(serve_handle* s, uint64_t ticket, int timeout_ms, odwf_result* res);
 
-/* Stop the loop after the running work, fail queued requests, free everything. */
+/*
+ * Admission policy.  admit_deadline_ms > 0: a request still waiting for admission after that
+ * long is shed, completing with ODWF_ETIMEOUT (its x is not written).  max_queued > 0: at most
+ * that many requests wait; serve_submit then answers ODWF_EBUSY and takes no ticket.  Values
+ * <= 0 disable either (the default).  Applies to requests already queued from the next loop pass.
+ */
+int serve_set_policy(serve_handle* s, double admit_deadline_ms, int max_queued);
+
+/*
+ * Cancel a request.  A queued request completes at once with ODWF_ECANCELED; a running one
+ * stops between two chunks of iterations (its systems' slots are freed, x is not written) and
+ * then completes with ODWF_ECANCELED.  A finished request keeps its status.  ODWF_ENOTFOUND
+ * for an unknown ticket.
+ */
+int serve_cancel(serve_handle* s, uint64_t ticket);
+
+/*
+ * Stop the loop after the running work, fail queued requests (ODWF_ETIMEOUT), finish pending
+ * copies of results to host buffers, free everything.  Any CUDA or solver error inside a batch
+ * fails every request with systems in that batch with the error's status (e.g. ODWF_ECUDA) and
+ * frees the batch; other batches continue.
+ */
 int serve_destroy(serve_handle* s);
 
 #ifdef __cplusplus

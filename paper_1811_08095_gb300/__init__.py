@@ -54,7 +54,7 @@ def _lattice(dims, t_antiperiodic):
     return lat
 
 
-def _params(tol, max_iter, prec, delta, system, link_recon, mq, check_every):
+def _params(tol, max_iter, prec, delta, system, link_recon, mq, check_every, link_prec="f32"):
     p = _lib.odwf_solve_params()
     p.tol = float(tol)
     p.max_iter = int(max_iter)
@@ -64,6 +64,7 @@ def _params(tol, max_iter, prec, delta, system, link_recon, mq, check_every):
     p.link_recon = int(link_recon)
     p.mq = float("nan") if mq is None else float(mq)
     p.check_every = int(check_every)
+    p.link_prec = PREC[link_prec] if isinstance(link_prec, str) else int(link_prec)
     return p
 
 
@@ -132,7 +133,8 @@ class Handle:
         check(self._lib.odwf_apply_m5(self._h, ptr(out), ptr(inp), int(n_sites), int(op), stream_ptr(stream)))
         return out
 
-    def mixed_cg_step(self, p_prev, r, x, outs, beta, rr, prec="f16", link_recon=12, mq=None, stream=None):
+    def mixed_cg_step(self, p_prev, r, x, outs, beta, rr, prec="f16", link_recon=12, mq=None, stream=None,
+                      link_prec="f32"):
         """odwf_mixed_cg_step: one production mixed CG iteration; `outs` is a list of 8 fields
         (or None) receiving p_prev as stored, p, chi_p, chi_t, a, c, r_new, x_new.  Returns the
         scalars as a dict."""
@@ -142,14 +144,27 @@ class Handle:
         sc.beta = float(beta)
         sc.rr = float(rr)
         pr = PREC[prec] if isinstance(prec, str) else int(prec)
-        check(self._lib.odwf_mixed_cg_step(self._h, pr, int(link_recon), self.mq if mq is None else float(mq),
+        lp = PREC[link_prec] if isinstance(link_prec, str) else int(link_prec)
+        check(self._lib.odwf_mixed_cg_step(self._h, pr, int(link_recon), lp, self.mq if mq is None else float(mq),
                                            ptr(p_prev), ptr(r), ptr(x), ctypes.cast(oa, ctypes.c_void_p),
                                            ctypes.byref(sc), stream_ptr(stream)))
         return {"pAp": sc.pAp, "alpha": sc.alpha, "rr_new": sc.rr_new, "status": sc.status}
 
+    def time_kernel(self, kind, fill, prec="f16", link_recon=12, link_prec="f32", nsys=1, reps=10, stream=None):
+        """odwf_time_kernel: CUDA-event time of `reps` launches of one production mixed kernel
+        (kind 1..4 = K1..K4, 5 = p update).  Returns the odwf_kernel_prof fields as a dict."""
+        out = _lib.odwf_kernel_prof()
+        pr = PREC[prec] if isinstance(prec, str) else int(prec)
+        lp = PREC[link_prec] if isinstance(link_prec, str) else int(link_prec)
+        check(self._lib.odwf_time_kernel(self._h, int(kind), pr, int(link_recon), lp, int(nsys), int(reps), ptr(fill),
+                                         ctypes.byref(out), stream_ptr(stream)))
+        return {"name": out.name.decode(), "launches": out.launches, "system_launches": out.system_launches,
+                "total_ms": out.total_ms, "bytes_per_system": out.bytes_per_system,
+                "bytes_per_launch": out.bytes_per_launch}
+
     def cg_solve(self, x, b, tol=1e-10, max_iter=100000, prec="f64", delta=0.01, system=ODWF_SYS_SCHUR_NORMAL,
-                 link_recon=12, mq=None, check_every=8, stream=None, raise_on_error=True):
-        p = _params(tol, max_iter, prec, delta, system, link_recon, mq, check_every)
+                 link_recon=12, mq=None, check_every=8, stream=None, raise_on_error=True, link_prec="f32"):
+        p = _params(tol, max_iter, prec, delta, system, link_recon, mq, check_every, link_prec)
         st = _lib.odwf_solve_stats()
         rc = self._lib.odwf_cg_solve(self._h, ptr(x), ptr(b), ctypes.byref(p), ctypes.byref(st), stream_ptr(stream))
         if raise_on_error:
@@ -159,7 +174,7 @@ class Handle:
         return d
 
     def cg_solve_batched(self, xs, bs, mqs=None, tol=1e-10, max_iter=100000, prec="f64", delta=0.01,
-                         link_recon=12, check_every=8, stream=None, raise_on_error=True):
+                         link_recon=12, check_every=8, stream=None, raise_on_error=True, link_prec="f32"):
         n = len(xs)
         assert len(bs) == n
         xa = (ctypes.c_void_p * n)(*[ptr(x).value for x in xs])
@@ -169,7 +184,7 @@ class Handle:
             mq_np = np.ascontiguousarray(mqs, dtype=np.float64)
             assert mq_np.shape == (n,)
             mq_arr = ptr(mq_np)
-        p = _params(tol, max_iter, prec, delta, ODWF_SYS_SCHUR_NORMAL, link_recon, None, check_every)
+        p = _params(tol, max_iter, prec, delta, ODWF_SYS_SCHUR_NORMAL, link_recon, None, check_every, link_prec)
         st = (_lib.odwf_solve_stats * n)()
         rc = self._lib.odwf_cg_solve_batched(self._h, n, ctypes.cast(xa, ctypes.c_void_p),
                                              ctypes.cast(ba, ctypes.c_void_p), mq_arr, ctypes.byref(p),
@@ -217,6 +232,19 @@ class Server:
         check(self._lib.serve_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
         self._keep[t.value] = (om, ba, xa, bs, xs)
         return t.value
+
+    def set_policy(self, admit_deadline_ms=0.0, max_queued=0):
+        check(self._lib.serve_set_policy(self._h, float(admit_deadline_ms), int(max_queued)))
+
+    def cancel(self, ticket):
+        check(self._lib.serve_cancel(self._h, ctypes.c_uint64(ticket)))
+
+    def try_submit(self, *a, **k):
+        """submit(), returning (status, ticket) instead of raising (ODWF_EBUSY when the queue is full)."""
+        try:
+            return _lib.ODWF_OK, self.submit(*a, **k)
+        except OdwfError as e:
+            return e.code, None
 
     def poll(self, ticket, timeout_ms=0):
         r = _lib.odwf_result()

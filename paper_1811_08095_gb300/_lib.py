@@ -17,14 +17,14 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libodwf.so")
 
 ODWF_OK, ODWF_EINVAL, ODWF_ENOMEM, ODWF_ENOCONV, ODWF_EBREAKDOWN, ODWF_ETIMEOUT, ODWF_ECUDA, ODWF_PENDING, \
-    ODWF_ENOTFOUND = range(9)
+    ODWF_ENOTFOUND, ODWF_ECANCELED, ODWF_EBUSY = range(11)
 ODWF_F64, ODWF_F32, ODWF_F16, ODWF_BF16 = range(4)
 ODWF_MODE_FULL, ODWF_MODE_SCHUR_EVEN = 0, 1
 ODWF_SYS_SCHUR_NORMAL, ODWF_SYS_FULL_NORMAL, ODWF_SYS_FULL_DIRAC = 0, 1, 2
 ODWF_OMEGA_SHIFTED_R5, ODWF_OMEGA_PLAIN = 0, 1
 
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOCONV", 4: "EBREAKDOWN", 5: "ETIMEOUT", 6: "ECUDA",
-                7: "PENDING", 8: "ENOTFOUND"}
+                7: "PENDING", 8: "ENOTFOUND", 9: "ECANCELED", 10: "EBUSY"}
 
 
 class odwf_lattice(ctypes.Structure):
@@ -34,7 +34,7 @@ class odwf_lattice(ctypes.Structure):
 class odwf_solve_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("delta", ctypes.c_double), ("system", ctypes.c_int32), ("link_recon", ctypes.c_int32),
-                ("mq", ctypes.c_double), ("check_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("mq", ctypes.c_double), ("check_every", ctypes.c_int32), ("link_prec", ctypes.c_int32)]
 
 
 class odwf_solve_stats(ctypes.Structure):
@@ -92,17 +92,20 @@ _SIGS = {
     "odwf_apply_normal_prec": ([P, P, P, I, I, P], I),
     "odwf_apply_m5": ([P, P, P, ctypes.c_long, I, P], I),
     "odwf_apply_m5_noalloc": ([I, D, D, P, P, P, ctypes.c_long, I, P], I),
-    "odwf_mixed_cg_step": ([P, I, I, D, P, P, P, P, ctypes.POINTER(odwf_cg_step_scalars), P], I),
+    "odwf_mixed_cg_step": ([P, I, I, I, D, P, P, P, P, ctypes.POINTER(odwf_cg_step_scalars), P], I),
     "odwf_cg_solve": ([P, P, P, ctypes.POINTER(odwf_solve_params), P, P], I),
     "odwf_cg_solve_batched": ([P, I, P, P, P, ctypes.POINTER(odwf_solve_params), P, P], I),
     "odwf_profile_enable": ([I], I),
     "odwf_profile_read": ([P, I, ctypes.POINTER(ctypes.c_int)], I),
     "odwf_launch_count": ([], ctypes.c_longlong),
+    "odwf_time_kernel": ([P, I, I, I, I, I, I, P, P, P], I),
     "serve_create": ([ctypes.c_size_t, ctypes.POINTER(P)], I),
     "serve_register_gauge": ([P, I, ctypes.POINTER(odwf_lattice), P], I),
     "serve_submit": ([P, ctypes.POINTER(odwf_request), ctypes.POINTER(ctypes.c_uint64)], I),
     "serve_poll": ([P, ctypes.c_uint64, I, ctypes.POINTER(odwf_result)], I),
     "serve_destroy": ([P], I),
+    "serve_set_policy": ([P, D, I], I),
+    "serve_cancel": ([P, ctypes.c_uint64], I),
 }
 
 

@@ -8,6 +8,11 @@
 
 namespace odwf {
 
+Lk link_format(const odwf_solve_params& prm) {
+    if (prm.link_prec == ODWF_F16) return Lk::H12;
+    return prm.link_recon == 18 ? Lk::F18 : Lk::F12;
+}
+
 void BatchCG::drop_graphs() {
     for (auto& kv : graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -36,7 +41,7 @@ HopParams<double> BatchCG::params<double>(int p_out) const {
 template <>
 HopParams<float> BatchCG::params<float>(int p_out) const {
     auto P = E->hop_params<float>(p_out, r_dev);
-    P.links = lk == Lk::F12 ? E->links_f12 : E->links_f18;
+    P.links = v2 ? E->links_site[(int)lk] : E->links_of(lk);
     P.st = st;
     P.partials = partials;
     P.counters = counters;
@@ -48,7 +53,7 @@ int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStr
     cap = capacity;
     mixed = prm.prec != ODWF_F64;
     low = (Sp)prm.prec;
-    lk = prm.link_recon == 18 ? Lk::F18 : Lk::F12;
+    lk = link_format(prm);
     delta = prm.delta > 0 ? prm.delta : 0.01;
     tol = prm.tol;
     max_iter = prm.max_iter;
@@ -70,7 +75,9 @@ int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStr
             return rc;
         if ((rc = E->ensure_links(lk, s))) return rc;
         v2 = hop2_supported(E->ns, low, E->vh());
+        if (lk == Lk::H12 && !v2) return fail(ODWF_EINVAL, "solve: FP16 links need Ns = 8 or 16");
         if (v2 && (rc = E->alloc_half(tag + ".X", low, cap, &Chil))) return rc;
+        if (v2 && (rc = E->ensure_site_links(lk, s))) return rc;
     }
     st = (SysState*)E->get_ws("cg.state", sizeof(SysState) * cap, &rc);
     if (rc) return rc;
@@ -109,17 +116,20 @@ int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStr
     const double n5 = (double)E->sites5();
     const double sp = !mixed ? 192.0 : (low == Sp::F32 ? 96.0 : 52.0);  // FP16/BF16: 48 + 4-byte scale
     const double acc = mixed ? 96.0 : 192.0;                              // r, x
-    const double links = 8.0 * (double)E->vh() * (!mixed ? 144.0 : (lk == Lk::F12 ? 48.0 : 72.0));
+    const double links = 8.0 * (double)E->vh() * (!mixed ? 144.0 : lk == Lk::F12 ? 48.0 : lk == Lk::H12 ? 24.0 : 72.0);
     const char* lowname[] = {"f64", "f32", "f16", "bf16"};
     const std::string pre = !mixed ? std::string("f64") :
-        std::string("mixed.") + lowname[(int)low] + (lk == Lk::F12 ? ".l12" : ".l18");
+        std::string("mixed.") + lowname[(int)low] + (lk == Lk::F12 ? ".l12" : lk == Lk::H12 ? ".lh12" : ".l18");
     if (v2) {
         const std::string p2 = pre + ".v2";
-        pcls[0] = prof_class(p2 + ".K1_chi_minv", n5 * 2 * sp, links);
-        pcls[1] = prof_class(p2 + ".K2_schur_norm_mdinv", n5 * 3 * sp, links);
-        pcls[2] = prof_class(p2 + ".K3_dag_minvdag", n5 * 2 * sp, links);
-        pcls[3] = prof_class(p2 + ".K4_normal_cg", n5 * (3 * sp + 4 * acc), links);
-        pcls[4] = prof_class(p2 + ".P_update_chi", n5 * (acc + 3 * sp), 0.0);
+        const char* kn[5] = {".K1_chi_minv", ".K2_schur_norm_mdinv", ".K3_dag_minvdag", ".K4_normal_cg", ".P_update_chi"};
+        const double ksys[5] = {n5 * 2 * sp, n5 * 3 * sp, n5 * 2 * sp, n5 * (3 * sp + 4 * acc), n5 * (acc + 3 * sp)};
+        for (int k = 0; k < 5; ++k) {
+            kname[k] = p2 + kn[k];
+            kbytes_sys[k] = ksys[k];
+            kbytes_launch[k] = k < 4 ? links : 0.0;
+            pcls[k] = prof_class(kname[k], kbytes_sys[k], kbytes_launch[k]);
+        }
     } else {
     pcls[0] = prof_class(pre + ".K1_minv", n5 * 2 * sp, links);
     pcls[1] = prof_class(pre + ".K2_schur_norm_mdinv", n5 * 3 * sp, links);
@@ -179,6 +189,16 @@ int BatchCG::release(int slot) {
     if (!bsrc.empty()) bsrc[slot] = nullptr;
     st_host[slot].status = kIdle;
     return ODWF_OK;
+}
+
+int BatchCG::cancel(int slot, cudaStream_t s) {
+    if (slot < 0 || slot >= cap) return fail(ODWF_EINVAL, "cancel: bad slot");
+    if (upd[slot]) {
+        ODWF_CK(cudaStreamWaitEvent(s, ev_rel[slot], 0));
+        upd[slot] = 0;
+    }
+    ODWF_CK(launch_state(st + slot, 1, 3, 0.0, s));
+    return release(slot);
 }
 
 int BatchCG::admit_internal(int slot, cudaStream_t s, double tol_slot, int max_iter_slot) {
@@ -356,6 +376,29 @@ int BatchCG::launch_iterations(int k, int lo, int n, cudaStream_t s) {
 
 // The four hops K1..K4 of one second-generation mixed iteration over slots lo..lo+n-1 (the
 // non-dagger hops read chi = B psi): the launches the solver replays every iteration.
+int BatchCG::launch_v2_kernel(int kind, int lo, int n, cudaStream_t s) {
+    if (kind == 5) return launch_v2_pupdate(1, lo, n, 1, kRunning, s);
+    auto P = params<float>(1);
+    P.gate = 1;
+    P.need_status = kRunning;
+    P.sys_base = lo;
+    const FieldRef ins[4] = {Chil.ref(), Tl.ref(), Al.ref(), Cl.ref()};
+    const FieldRef outs[4] = {Tl.ref(), Al.ref(), Cl.ref(), FieldRef{}};
+    const FieldRef zs[4] = {FieldRef{}, Pl.ref(), FieldRef{}, Al.ref()};
+    const int k = kind - 1;
+    P.p_out = (k & 1) ? 0 : 1;
+    P.in = ins[k];
+    P.out = outs[k];
+    P.z = zs[k];
+    if (k == 3) {
+        P.cg_r = Rin.ref();
+        P.cg_x = Xin.ref();
+        P.cg_p = Pl.ref();
+    }
+    ODWF_CK(launch_hop2(P, kind, low, lk, n, s));
+    return ODWF_OK;
+}
+
 int BatchCG::launch_v2_hops(int lo, int n, cudaStream_t s) {
     auto P = params<float>(1);
     P.gate = 1;

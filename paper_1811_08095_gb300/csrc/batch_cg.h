@@ -26,12 +26,16 @@
 
 #include <chrono>
 #include <map>
+#include <string>
 #include <vector>
 
 #include "engine.h"
 #include "profile.h"
 
 namespace odwf {
+
+// inner link format of a mixed-precision solve (link_recon, link_prec of the parameters)
+Lk link_format(const odwf_solve_params& prm);
 
 struct BatchCG {
     Engine* E = nullptr;
@@ -76,6 +80,8 @@ struct BatchCG {
     };
     std::map<unsigned long long, GraphEntry> graphs;
     int pcls[5] = {-1, -1, -1, -1, -1};  // profiler classes: K1..K4, p update
+    std::string kname[5];                 // (second-generation kernels) class names and
+    double kbytes_sys[5] = {0}, kbytes_launch[5] = {0};  // algorithmic bytes per system / launch
     int pcls_rel[4] = {-1, -1, -1, -1};  // FP64 residual hops of the reliable update
 
     ~BatchCG();
@@ -90,6 +96,9 @@ struct BatchCG {
               int max_iter_slot = 0);
     int admit_internal(int slot, cudaStream_t s, double tol_slot = 0, int max_iter_slot = 0);  // B64[slot] filled
     int release(int slot);  // slot free for the next admit
+    // stop a running slot between chunks (its device status becomes idle, after any reliable
+    // update in flight) and free it; its solution is not written out
+    int cancel(int slot, cudaStream_t s);
     int run_iterations(int k, cudaStream_t s);
     int resume(cudaStream_t s, bool block);          // rejoin slots whose update finished
     int poll(cudaStream_t s);                      // refresh st_host (synchronizes s)
@@ -98,6 +107,7 @@ struct BatchCG {
     // second-generation mixed iteration pieces (v2 only): K1..K4 hops, and the p update
     int launch_v2_hops(int lo, int n, cudaStream_t s);
     int launch_v2_pupdate(int mode, int lo, int n, int gate, int need, cudaStream_t s);
+    int launch_v2_kernel(int kind, int lo, int n, cudaStream_t s);  // kind 1..4: K1..K4 alone, 5: P
     // write a slot's scalars (and r = m_q / (2 m0)) directly; synchronizes s
     int set_state(int slot, const SysState& init, double r, cudaStream_t s);
     bool slot_running(int i) const;

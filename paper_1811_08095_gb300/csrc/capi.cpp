@@ -130,14 +130,23 @@ int odwf_apply_m5(odwf_handle* h, void* out, const void* in, long n_sites, int o
     GUARD_END
 }
 
-int odwf_mixed_cg_step(odwf_handle* h, int prec, int link_recon, double mq, const void* p_prev, const void* r,
+int odwf_mixed_cg_step(odwf_handle* h, int prec, int link_recon, int link_prec, double mq, const void* p_prev, const void* r,
                        const void* x, void* const* outs, odwf_cg_step_scalars* sc, void* stream) {
     GUARD_BEGIN
     if (!h) return fail(ODWF_EINVAL, "odwf_mixed_cg_step: null handle");
     ON_DEVICE(h, "odwf_mixed_cg_step", p_prev, r, x);
     if (outs)
         for (int i = 0; i < 8; ++i) ON_DEVICE(h, "odwf_mixed_cg_step", outs[i]);
-    return h->e.mixed_cg_step(prec, link_recon, mq, p_prev, r, x, outs, sc, (cudaStream_t)stream);
+    return h->e.mixed_cg_step(prec, link_recon, link_prec, mq, p_prev, r, x, outs, sc, (cudaStream_t)stream);
+    GUARD_END
+}
+
+int odwf_time_kernel(odwf_handle* h, int kind, int prec, int link_recon, int link_prec, int nsys, int reps,
+                     const void* fill, odwf_kernel_prof* out, void* stream) {
+    GUARD_BEGIN
+    if (!h) return fail(ODWF_EINVAL, "odwf_time_kernel: null handle");
+    ON_DEVICE(h, "odwf_time_kernel", fill);
+    return h->e.time_kernel(kind, prec, link_recon, link_prec, nsys, reps, fill, out, (cudaStream_t)stream);
     GUARD_END
 }
 

@@ -43,7 +43,7 @@ int emit(Engine* E, Sp sp, const FieldRef& f, int p, void* dst, cudaStream_t st)
 
 }  // namespace
 
-int Engine::mixed_cg_step(int prec, int recon, double mq_step, const void* p_prev, const void* r, const void* x,
+int Engine::mixed_cg_step(int prec, int recon, int link_prec, double mq_step, const void* p_prev, const void* r, const void* x,
                           void* const* outs, odwf_cg_step_scalars* sc, cudaStream_t st) {
     if (!gauge_set) return fail(ODWF_EINVAL, "odwf_mixed_cg_step: gauge field not set");
     if (!p_prev || !r || !x || !outs || !sc) return fail(ODWF_EINVAL, "odwf_mixed_cg_step: null argument");
@@ -51,6 +51,10 @@ int Engine::mixed_cg_step(int prec, int recon, double mq_step, const void* p_pre
         return fail(ODWF_EINVAL, "odwf_mixed_cg_step: prec must be F32, F16 or BF16");
     if (recon == 0) recon = 12;
     if (recon != 12 && recon != 18) return fail(ODWF_EINVAL, "odwf_mixed_cg_step: link_recon must be 12 or 18");
+    if (link_prec != 0 && link_prec != ODWF_F32 && link_prec != ODWF_F16)
+        return fail(ODWF_EINVAL, "odwf_mixed_cg_step: link_prec must be 0, ODWF_F32 or ODWF_F16");
+    if (link_prec == ODWF_F16 && recon != 12)
+        return fail(ODWF_EINVAL, "odwf_mixed_cg_step: FP16 links are stored with 12 reals");
     if (!std::isfinite(mq_step)) return fail(ODWF_EINVAL, "odwf_mixed_cg_step: non-finite m_q");
     if (!(sc->rr > 0.0) || !std::isfinite(sc->rr) || !std::isfinite(sc->beta))
         return fail(ODWF_EINVAL, "odwf_mixed_cg_step: rr must be positive and finite, beta finite");
@@ -65,6 +69,7 @@ int Engine::mixed_cg_step(int prec, int recon, double mq_step, const void* p_pre
     prm.delta = 0.01;
     prm.system = ODWF_SYS_SCHUR_NORMAL;
     prm.link_recon = recon;
+    prm.link_prec = link_prec;
     BatchCG bc;
     int rc = bc.init(this, 1, prm, st, 0);
     if (rc) return rc;
@@ -107,6 +112,72 @@ int Engine::mixed_cg_step(int prec, int recon, double mq_step, const void* p_pre
     sc->alpha = S.alpha;
     sc->rr_new = S.rr_new;
     sc->status = S.status == kBreakdown ? ODWF_EBREAKDOWN : ODWF_OK;
+    return ODWF_OK;
+}
+
+int Engine::time_kernel(int kind, int prec, int recon, int link_prec, int nsys, int reps, const void* fill,
+                        odwf_kernel_prof* out, cudaStream_t st) {
+    if (!gauge_set) return fail(ODWF_EINVAL, "odwf_time_kernel: gauge field not set");
+    if (!fill || !out) return fail(ODWF_EINVAL, "odwf_time_kernel: null argument");
+    if (kind < 1 || kind > 5) return fail(ODWF_EINVAL, "odwf_time_kernel: kind must be 1..5");
+    if (nsys < 1 || nsys > 64 || reps < 1) return fail(ODWF_EINVAL, "odwf_time_kernel: need 1 <= nsys <= 64, reps >= 1");
+    if (prec != ODWF_F32 && prec != ODWF_F16 && prec != ODWF_BF16)
+        return fail(ODWF_EINVAL, "odwf_time_kernel: prec must be F32, F16 or BF16");
+    if (recon == 0) recon = 12;
+    odwf_solve_params prm;
+    std::memset(&prm, 0, sizeof(prm));
+    prm.tol = 1e-10;
+    prm.max_iter = INT_MAX;
+    prm.prec = prec;
+    prm.delta = 0.01;
+    prm.link_recon = recon;
+    prm.link_prec = link_prec;
+    BatchCG bc;
+    int rc = bc.init(this, nsys, prm, st, 0);
+    if (rc) return rc;
+    if (!bc.v2) return fail(ODWF_EINVAL, "odwf_time_kernel: the production mixed kernels need Ns = 8 or 16");
+    const double2* fd = nullptr;
+    if ((rc = stage_field(this, fill, ext_bytes(ODWF_MODE_SCHUR_EVEN), "step.p", st, &fd))) return rc;
+    const Sp low = (Sp)prec;
+    SysState s0;
+    std::memset(&s0, 0, sizeof(s0));
+    s0.rr = 1.0;
+    s0.beta = 0.5;
+    s0.alpha = 0.1;
+    s0.r_max = 1.0;
+    s0.bb = 1.0;
+    s0.rscale = 1.0;
+    s0.status = kRunning;
+    s0.max_iter = INT_MAX;
+    s0.reliable = 1;
+    for (int i = 0; i < nsys; ++i) {
+        const HalfField* lows[5] = {&bc.Pl, &bc.Tl, &bc.Al, &bc.Cl, &bc.Chil};
+        for (const HalfField* f : lows) ODWF_CK(launch_pack(low, fd, f->ref_sys(i), g, 0, ns, 1, st));
+        ODWF_CK(launch_pack(Sp::F32, fd, bc.Rin.ref_sys(i), g, 0, ns, 1, st));
+        ODWF_CK(launch_pack(Sp::F32, fd, bc.Xin.ref_sys(i), g, 0, ns, 1, st));
+        if ((rc = bc.set_state(i, s0, mq / (2.0 * m0), st))) return rc;
+    }
+    if ((rc = bc.launch_v2_kernel(kind, 0, nsys, st))) return rc;  // warm-up launch
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ODWF_CK(cudaEventCreate(&e0));
+    ODWF_CK(cudaEventCreate(&e1));
+    float ms = 0.f;
+    cudaError_t ce = cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && ce == cudaSuccess && !rc; ++r) rc = bc.launch_v2_kernel(kind, 0, nsys, st);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (ce != cudaSuccess) return cuda_fail(ce, "odwf_time_kernel: events");
+    std::memset(out, 0, sizeof(*out));
+    std::strncpy(out->name, bc.kname[kind - 1].c_str(), sizeof(out->name) - 1);
+    out->launches = reps;
+    out->system_launches = (int64_t)reps * nsys;
+    out->total_ms = ms;
+    out->bytes_per_system = bc.kbytes_sys[kind - 1];
+    out->bytes_per_launch = bc.kbytes_launch[kind - 1];
     return ODWF_OK;
 }
 

@@ -50,6 +50,9 @@ Engine::~Engine() {
     if (links_d18) cudaFree(links_d18);
     if (links_f18) cudaFree(links_f18);
     if (links_f12) cudaFree(links_f12);
+    if (links_h12) cudaFree(links_h12);
+    for (void* p : links_site)
+        if (p) cudaFree(p);
     if (nbr) cudaFree(nbr);
     if (pinned) cudaFreeHost(pinned);
 }
@@ -177,7 +180,8 @@ int Engine::set_gauge(const void* U, cudaStream_t st) {
     if (!links_d18) ODWF_CK(cudaMalloc(&links_d18, nl * 144));
     ODWF_CK(launch_pack_links(Ud, links_d18, nullptr, nullptr, g, st));
     // FP32 copies are derived from the FP64 ones on first use (ensure_links)
-    have_f12 = have_f18 = false;
+    have_f12 = have_f18 = have_h12 = false;
+    for (bool& b : have_site) b = false;
     if (!is_device_ptr(U)) {
         ODWF_CK(cudaStreamSynchronize(st));
         auto it = ws.find("gauge_stage");  // the staging copy is only needed during packing
@@ -205,7 +209,23 @@ int Engine::ensure_links(Lk lk, cudaStream_t st) {
         if (!links_f18) ODWF_CK(cudaMalloc(&links_f18, nl * 80));
         ODWF_CK(launch_links_from_d18(links_d18, links_f18, nullptr, nl, st));
         have_f18 = true;
+    } else if (lk == Lk::H12 && !have_h12) {
+        if (!links_h12) ODWF_CK(cudaMalloc(&links_h12, nl * 24));
+        ODWF_CK(launch_links_h12_from_d18(links_d18, links_h12, nl, st));
+        have_h12 = true;
     }
+    return ODWF_OK;
+}
+
+int Engine::ensure_site_links(Lk lk, cudaStream_t st) {
+    int rc = ensure_links(lk, st);
+    if (rc) return rc;
+    const int k = (int)lk;
+    if (have_site[k]) return ODWF_OK;
+    const int bytes = lk == Lk::F12 ? 48 : lk == Lk::F18 ? 80 : lk == Lk::H12 ? 24 : 144;
+    if (!links_site[k]) ODWF_CK(cudaMalloc(&links_site[k], 16 * vh() * (size_t)bytes));
+    ODWF_CK(launch_links_site_major(links_of(lk), links_site[k], bytes, nbr, g, st));
+    have_site[k] = true;
     return ODWF_OK;
 }
 
@@ -479,6 +499,10 @@ static int check_params(const odwf_solve_params* prm) {
     if (prm->prec < ODWF_F64 || prm->prec > ODWF_BF16) return fail(ODWF_EINVAL, "solve: bad prec");
     if (prm->link_recon != 0 && prm->link_recon != 12 && prm->link_recon != 18)
         return fail(ODWF_EINVAL, "solve: link_recon must be 0, 12 or 18");
+    if (prm->link_prec != 0 && prm->link_prec != ODWF_F32 && prm->link_prec != ODWF_F16)
+        return fail(ODWF_EINVAL, "solve: link_prec must be 0, ODWF_F32 or ODWF_F16");
+    if (prm->link_prec == ODWF_F16 && prm->link_recon == 18)
+        return fail(ODWF_EINVAL, "solve: FP16 links are stored with 12 reals (link_recon 0 or 12)");
     return ODWF_OK;
 }
 

@@ -63,9 +63,15 @@ struct Engine {
     void* links_d18 = nullptr;
     void* links_f18 = nullptr;
     void* links_f12 = nullptr;
+    void* links_h12 = nullptr;
+    void* links_site[4] = {nullptr, nullptr, nullptr, nullptr};  // site-major copies by Lk (second-generation hops)
+    bool have_site[4] = {false, false, false, false};
     int* nbr = nullptr;  // neighbour table of the second-generation hops (launch_build_neighbours)
     bool gauge_set = false;
-    bool have_f12 = false, have_f18 = false;  // FP32 link copies derived from the FP64 ones
+    bool have_f12 = false, have_f18 = false, have_h12 = false;  // low-precision copies of the FP64 links
+    const void* links_of(Lk lk) const {
+        return lk == Lk::F12 ? links_f12 : lk == Lk::F18 ? links_f18 : lk == Lk::H12 ? links_h12 : links_d18;
+    }
 
     // named workspaces (grow-only)
     std::map<std::string, DevBuf> ws;
@@ -76,6 +82,7 @@ struct Engine {
     int init(const odwf_lattice* l, int Ns, double m0_, double mq_, const double* w);
     int set_gauge(const void* U, cudaStream_t st);
     int ensure_links(Lk lk, cudaStream_t st);  // FP32 links in format lk, converted on first use
+    int ensure_site_links(Lk lk, cudaStream_t st);  // site-major copy of format lk (after ensure_links)
 
     size_t vh() const { return (size_t)g.Vh; }
     size_t sites5() const { return (size_t)g.Vh * ns; }
@@ -101,8 +108,10 @@ struct Engine {
     int apply_normal(void* out, const void* in, int system, cudaStream_t st);
     int apply_m5(void* out, const void* in, long n_sites, int op, cudaStream_t st);
     int apply_low_normal(void* out, const void* in, int prec, int recon, cudaStream_t st);
-    int mixed_cg_step(int prec, int recon, double mq_step, const void* p_prev, const void* r, const void* x,
+    int mixed_cg_step(int prec, int recon, int link_prec, double mq_step, const void* p_prev, const void* r, const void* x,
                       void* const* outs, odwf_cg_step_scalars* sc, cudaStream_t st);
+    int time_kernel(int kind, int prec, int recon, int link_prec, int nsys, int reps, const void* fill,
+                    odwf_kernel_prof* out, cudaStream_t st);
     int solve(int nsys, void* const* x, const void* const* b, const double* mq_arr, const odwf_solve_params* prm,
               odwf_solve_stats* stats, cudaStream_t st);
     int solve_on(int nsys, void* const* x, const void* const* b, const double* mq_arr,

@@ -8,7 +8,7 @@
 namespace odwf {
 
 enum class Sp { F64 = 0, F32 = 1, F16 = 2, BF16 = 3 };
-enum class Lk { D18 = 0, F18 = 1, F12 = 2 };
+enum class Lk { D18 = 0, F18 = 1, F12 = 2, H12 = 3 };
 
 struct FieldRef;
 template <class R>
@@ -80,6 +80,14 @@ cudaError_t launch_pack_links(const double2* U, void* d18, void* f18, void* f12,
 
 // FP32 links (18 reals padded to 20, or the first two rows) from the packed FP64 links
 cudaError_t launch_links_from_d18(const void* d18, void* f18, void* f12, size_t n_links, cudaStream_t st);
+// FP16 links of 12 reals (rows 0, 1, round to nearest) from the packed FP64 links
+cudaError_t launch_links_h12_from_d18(const void* d18, void* h12, size_t n_links, cudaStream_t st);
+// Site-major copy of a link array for the second-generation hops: for each parity p and half
+// site h the eight links that site's hops multiply by, contiguous: out[(p * Vh + h) * 8 + j] =
+// U_mu(x) (j = 2 mu, forward) or U_mu(x - mu) (j = 2 mu + 1, backward), `bytes` per link, gathered
+// from the standard [p][mu][h] array `in` through the neighbour table (both parities).
+cudaError_t launch_links_site_major(const void* in, void* out, int bytes, const int* nbr, const Geom& g,
+                                    cudaStream_t st);
 // Neighbour table: for each parity p and half site h, the half indices of the eight
 // neighbours (x+, x-, y+, y-, z+, z-, t+, t-) in the other parity, bit 31 set where the hop
 // crosses the antiperiodic time boundary.  nbr[(p * Vh + h) * 8 + j], 2 * Vh * 8 ints.

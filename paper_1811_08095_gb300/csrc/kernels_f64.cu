@@ -167,9 +167,12 @@ __global__ void state_kernel(SysState* st, int nsys, int mode, double tol2) {
         }
         S.iter = 0;
         S.alpha = S.beta = 0.0;
-        S.status = (S.sum > 0.0) ? kRunning : kDone;
+        // a non-finite right-hand side (NaN / Inf in b) is a breakdown, not a converged b = 0
+        S.status = !isfinite(S.sum) ? kBreakdown : (S.sum > 0.0) ? kRunning : kDone;
     } else if (mode == 2) {
         if (S.status == kRestarting) S.status = kRunning;
+    } else if (mode == 3) {
+        S.status = kIdle;  // cancelled: every gated kernel skips the slot from now on
     } else {
         if (S.status != kNeedUpdate) return;
         const double rt = S.sum;  // true |r|^2 of the recomputed residual
@@ -265,6 +268,39 @@ cudaError_t launch_links_from_d18(const void* d18, void* f18, void* f12, size_t 
     note_launch();
     links_from_d18_kernel<<<blocks_for(n_links, 256), 256, 0, st>>>((const double*)d18, (float*)f18, (float*)f12,
                                                                      n_links);
+    return cudaGetLastError();
+}
+
+__global__ void links_h12_from_d18_kernel(const double* __restrict__ d18, __half2* h12, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* src = d18 + i * 18;
+    for (int k = 0; k < 6; ++k) h12[i * 6 + k] = __halves2half2(__double2half(src[2 * k]), __double2half(src[2 * k + 1]));
+}
+
+cudaError_t launch_links_h12_from_d18(const void* d18, void* h12, size_t n_links, cudaStream_t st) {
+    note_launch();
+    links_h12_from_d18_kernel<<<blocks_for(n_links, 256), 256, 0, st>>>((const double*)d18, (__half2*)h12, n_links);
+    return cudaGetLastError();
+}
+
+__global__ void links_site_major_kernel(const uint2* __restrict__ in, uint2* __restrict__ out, int words,
+                                        const int* __restrict__ nbr, Geom g) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (p * Vh + h) * 8 + j
+    if (i >= 16 * (size_t)g.Vh) return;
+    const int j = (int)(i & 7);
+    const size_t ph = i >> 3;
+    const int p = (int)(ph / g.Vh), h = (int)(ph % g.Vh), mu = j >> 1;
+    const size_t src = (j & 1) == 0 ? ((size_t)(p * 4 + mu) * g.Vh + h)
+                                    : ((size_t)((1 - p) * 4 + mu) * g.Vh + (nbr[ph * 8 + j] & 0x7fffffff));
+    for (int w = 0; w < words; ++w) out[i * words + w] = in[src * words + w];
+}
+
+cudaError_t launch_links_site_major(const void* in, void* out, int bytes, const int* nbr, const Geom& g,
+                                    cudaStream_t st) {
+    note_launch();
+    links_site_major_kernel<<<blocks_for(16 * (size_t)g.Vh, 256), 256, 0, st>>>((const uint2*)in, (uint2*)out, bytes / 8,
+                                                                               nbr, g);
     return cudaGetLastError();
 }
 

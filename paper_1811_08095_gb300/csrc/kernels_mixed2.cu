@@ -8,7 +8,8 @@
 //   K2  s = p - M^-1 (-1/2 W chi_t);  |s|^2 -> alpha;  a = M^-dag s    (s = S p)
 //   K3  c = M^-dag (-1/2 B^dag W^dag a)
 //   K4  A p = M^dag a + 1/2 B^dag W^dag c;  r -= alpha A p;  x += alpha p;  |r|^2 -> beta
-// The eight links of an output site are loaded (and, for 12-real storage, completed to
+// The eight links of an output site (stored contiguously per site, see launch_links_site_major)
+// are loaded (and, for 12-real storage, completed to
 // 18 reals) once per site: lane d < 8 of the site's lane group handles direction d and
 // leaves it in shared memory, which the group's Ns lanes then read (the group lies in one
 // warp, so a warp barrier suffices).  The per-site FP16/BF16 scale and the time-boundary
@@ -101,15 +102,16 @@ __device__ __forceinline__ void unpack_site(const RawSite<SP>& r, float2 Ur[3], 
 // gamma_mu = [[0, G], [G^dag, 0]]); W = U H (or U^dag H); then
 //   AU += sc W,  lower spins += sg sc G^dag W,
 // accumulated in AD (order (2, 3)) for mu = 2, 3 and in ADS (order (3, 2)) for mu = 0, 1, so
-// that no pair ever needs its halves exchanged.  The link comes from shared memory as nine
-// float4 (ur, ur, ui, ui), element (a, b) at index 3a + b.
-// Link source for hop_dir_packed: element (a, b) of U as broadcast pairs (ur, ur), (ui, ui).
-struct LinkStaged {  // nine float4 (ur, ur, ui, ui) in shared memory
-    const float4* q;
+// that no pair ever needs its halves exchanged.  The link source returns element (a, b) of U
+// as the broadcast pairs (ur, ur), (ui, ui).
+// Link source for hop_dir_packed: nine float2 (ur, ui) in shared memory, element (a, b) at
+// index 3a + b, returned as the broadcast pairs (ur, ur), (ui, ui) that the spin-pair FMAs need.
+struct LinkStaged2 {
+    const float2* q;
     __device__ __forceinline__ void get(int a, int b, float2& ur, float2& ui) const {
-        const float4 v = q[3 * a + b];
-        ur = make_float2(v.x, v.y);
-        ui = make_float2(v.z, v.w);
+        const float2 v = q[3 * a + b];
+        ur = make_float2(v.x, v.x);
+        ui = make_float2(v.y, v.y);
     }
 };
 template <class SP, int MU, bool DAGU, class LF>
@@ -182,11 +184,122 @@ __device__ __forceinline__ void hop_dir_packed(const RawSite<SP>& raw, float sc_
     }
 }
 
-constexpr int kLinkStride = 36;                  // floats per staged link: 9 x (ur, ur, ui, ui)
-constexpr int kSiteLinks = 8 * kLinkStride + 4;  // floats per site (padding spreads banks)
+// ---------------------------------------------------------------- fifth-dimension epilogue on spin pairs
+// One chirality half of a 5D site in the hop's own register layout: for colour c,
+// R[c] = (spin_a.re, spin_b.re), I[c] = (spin_a.im, spin_b.im); up = spins (0, 1), down = (2, 3).
+// The fifth-dimension operators act identically on all twelve reals of a chirality, so they run
+// on these pairs directly (packed FMAs, no repacking into memory order).
+struct Half6 {
+    float2 R[3], I[3];
+    __device__ __forceinline__ float2& p(int k) { return k < 3 ? R[k] : I[k - 3]; }
+};
+
+__device__ __forceinline__ float2 shfl2_idx(float2 v, int src, int w) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src, w), __shfl_sync(0xffffffffu, v.y, src, w));
+}
+__device__ __forceinline__ float2 shfl2_up(float2 v, int d, int w) {
+    return make_float2(__shfl_up_sync(0xffffffffu, v.x, d, w), __shfl_up_sync(0xffffffffu, v.y, d, w));
+}
+__device__ __forceinline__ float2 shfl2_down(float2 v, int d, int w) {
+    return make_float2(__shfl_down_sync(0xffffffffu, v.x, d, w), __shfl_down_sync(0xffffffffu, v.y, d, w));
+}
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// Bidiagonal X = diag(a) + diag(b) L (dag = false) or its adjoint a + L^dag b (dag = true) on both
+// chiralities (L: up from s-1, down from s+1, corners -r; L^dag the reverse), as bidiag_apply.
+template <int NS>
+__device__ __forceinline__ void bidiag_pairs(Half6& up, Half6& dn, float a_s, float b_s, float r, int s, bool dag) {
+    const int sm = (s + NS - 1) & (NS - 1), sp = (s + 1) & (NS - 1);
+    if (!dag) {
+        const float2 cm = f2(s == 0 ? -r * b_s : b_s), cp = f2(s == NS - 1 ? -r * b_s : b_s);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float2 u = shfl2_idx(up.p(k), sm, NS), d = shfl2_idx(dn.p(k), sp, NS);
+            up.p(k) = fma2(f2(a_s), up.p(k), __fmul2_rn(cm, u));
+            dn.p(k) = fma2(f2(a_s), dn.p(k), __fmul2_rn(cp, d));
+        }
+    } else {
+        const float2 cu = f2(s == NS - 1 ? -r : 1.f), cd = f2(s == 0 ? -r : 1.f);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float2 u = shfl2_idx(__fmul2_rn(f2(b_s), up.p(k)), sp, NS);
+            const float2 d = shfl2_idx(__fmul2_rn(f2(b_s), dn.p(k)), sm, NS);
+            up.p(k) = fma2(cu, u, __fmul2_rn(f2(a_s), up.p(k)));
+            dn.p(k) = fma2(cd, d, __fmul2_rn(f2(a_s), dn.p(k)));
+        }
+    }
+}
+
+// Cyclic bidiagonal solve along s of pre * v on one chirality (six pairs), as cyclic_solve12:
+//   forward:  d_s w_s + c_s w_{s-1} = pre v_s,  w_{-1} := -r w_{Ns-1}
+//   backward: d_s w_s + c_s w_{s+1} = pre v_s,  w_{Ns} := -r w_0
+template <int NS>
+__device__ __forceinline__ void cyclic_pairs(Half6& v, float pre, float inv_d, float c_s, float r, int s, bool fwd) {
+    float coef = -c_s * inv_d;
+    const float2 sc = f2(pre * inv_d);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v.p(k) = __fmul2_rn(sc, v.p(k));
+    const int q = fwd ? s : NS - 1 - s;
+#pragma unroll
+    for (int off = 1; off < NS; off <<= 1) {
+        const float pc = fwd ? __shfl_up_sync(0xffffffffu, coef, off, NS) : __shfl_down_sync(0xffffffffu, coef, off, NS);
+        const float2 cm = f2(q >= off ? coef : 0.f);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float2 pv = fwd ? shfl2_up(v.p(k), off, NS) : shfl2_down(v.p(k), off, NS);
+            v.p(k) = fma2(cm, pv, v.p(k));
+        }
+        if (q >= off) coef *= pc;
+    }
+    const int last = fwd ? NS - 1 : 0;
+    const float Al = __shfl_sync(0xffffffffu, coef, last, NS);
+    const float2 cf = f2(coef * (-r / (1.f + r * Al)));
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v.p(k) = fma2(cf, shfl2_idx(v.p(k), last, NS), v.p(k));
+}
+
+// M^-1 (dag = false) or M^-dag (dag = true) of pre * v, as minv_apply
+template <int NS>
+__device__ __forceinline__ void minv_pairs(Half6& up, Half6& dn, const Coef5<float>& cf, float r, int s, bool dag,
+                                           float pre) {
+    const float inv_d = cf.inv_d[s];
+    if (!dag) {
+        cyclic_pairs<NS>(up, pre, inv_d, cf.e[s], r, s, true);
+        cyclic_pairs<NS>(dn, pre, inv_d, cf.e[s], r, s, false);
+    } else {
+        cyclic_pairs<NS>(up, pre, inv_d, cf.e[(s + 1) & (NS - 1)], r, s, false);
+        cyclic_pairs<NS>(dn, pre, inv_d, cf.e[(s + NS - 1) & (NS - 1)], r, s, true);
+    }
+}
+
+// memory order [spin][colour][re, im] <-> pairs
+__device__ __forceinline__ void pairs_to_mem(const Half6& up, const Half6& dn, float v[24]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        v[2 * c] = up.R[c].x;
+        v[2 * c + 1] = up.I[c].x;
+        v[6 + 2 * c] = up.R[c].y;
+        v[6 + 2 * c + 1] = up.I[c].y;
+        v[12 + 2 * c] = dn.R[c].x;
+        v[12 + 2 * c + 1] = dn.I[c].x;
+        v[18 + 2 * c] = dn.R[c].y;
+        v[18 + 2 * c + 1] = dn.I[c].y;
+    }
+}
+__device__ __forceinline__ void mem_to_pairs(const float v[24], Half6& up, Half6& dn) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        up.R[c] = make_float2(v[2 * c], v[6 + 2 * c]);
+        up.I[c] = make_float2(v[2 * c + 1], v[6 + 2 * c + 1]);
+        dn.R[c] = make_float2(v[12 + 2 * c], v[18 + 2 * c]);
+        dn.I[c] = make_float2(v[12 + 2 * c + 1], v[18 + 2 * c + 1]);
+    }
+}
 
 template <class SP, class LK, int NS, int KIND>
 __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P) {
+    constexpr int kLS = 18;            // floats per staged link: 9 x (ur, ui)
+    constexpr int kSL = 8 * kLS + 4;   // floats per site (padding spreads banks)
     constexpr bool DAG = (KIND == K3 || KIND == K4);
     const int sys = blockIdx.y + P.sys_base;
     if (P.gate && P.st[sys].status != P.need_status) return;
@@ -198,7 +311,7 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
     const bool valid = hh < (size_t)P.g.Vh;
     const int h = valid ? (int)hh : 0;
     const float r = (float)P.r_sys[sys];
-    const int p_out = P.p_out, p_in = 1 - p_out;
+    const int p_out = P.p_out;
 
     // the eight neighbours of this site (half index) and their time-boundary signs (bit j)
     int nb[8];
@@ -214,18 +327,18 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
         }
     }
 
-    // stage the site's eight links in shared memory: lane d < 8 of the group loads direction d
-    __shared__ __align__(16) float s_links[(kBS2 / NS) * kSiteLinks];
-    float* my_links = s_links + (threadIdx.x / NS) * kSiteLinks;
+    // stage the site's eight links in shared memory as (ur, ui) pairs: lane d < 8 of the group
+    // loads direction d from the site-major link array (the eight links of a site are contiguous,
+    // so the loads neither wait for the neighbour table nor scatter); the group's Ns lanes then
+    // read them (the group lies in one warp)
+    __shared__ __align__(16) float s_links[(kBS2 / NS) * kSL];
+    float* my_links = s_links + (threadIdx.x / NS) * kSL;
     if (s < 8) {
-        const int mu = s >> 1, dir = s & 1;
-        const size_t lidx = dir == 0 ? ((size_t)(p_out * 4 + mu) * P.g.Vh + h)
-                                     : ((size_t)(p_in * 4 + mu) * P.g.Vh + nb[s]);
         float u[18];
-        LinkIO<LK, float>::load(P.links, lidx, u);
-        float4* dst = reinterpret_cast<float4*>(my_links + s * kLinkStride);
+        LinkIO<LK, float>::load(P.links, ((size_t)p_out * P.g.Vh + h) * 8 + s, u);
+        float2* dst = reinterpret_cast<float2*>(my_links + s * kLS);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) dst[k] = make_float4(u[2 * k], u[2 * k], u[2 * k + 1], u[2 * k + 1]);
+        for (int k = 0; k < 9; ++k) dst[k] = make_float2(u[2 * k], u[2 * k + 1]);
     }
     __syncwarp();
 
@@ -234,7 +347,7 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
     float2 AUr[3], AUi[3], ADr[3], ADi[3], ADSr[3], ADSi[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) AUr[c] = AUi[c] = ADr[c] = ADi[c] = ADSr[c] = ADSi[c] = make_float2(0.f, 0.f);
-    const float4* L4 = reinterpret_cast<const float4*>(my_links);
+    const float2* L2p = reinterpret_cast<const float2*>(my_links);
     // forward hops use (1 - gamma) for D and (1 + gamma) for D^dag; backward the opposite
     constexpr float SF = DAG ? 1.f : -1.f;
     // neighbour j + 1 is fetched before neighbour j is processed
@@ -245,7 +358,7 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
         constexpr int j_ = 2 * MU_ + DIR_;                                                                        \
         if (j_ < 7) fetch_site<SP>(in, in_n, (unsigned)nb[j_ + 1 < 8 ? j_ + 1 : 7], s, NS, rs[(j_ + 1) & 1]);        \
         const float sgn_ = (flip & (1u << j_)) ? -1.f : 1.f;                                                     \
-        const LinkStaged ls_{L4 + j_ * 9};                                                                        \
+        const LinkStaged2 ls_{L2p + j_ * 9};                                                                      \
         hop_dir_packed<SP, MU_, DIR_ == 1>(rs[j_ & 1], sgn_, DIR_ == 0 ? SF : -SF, ls_, AUr, AUi, ADr, ADi, ADSr,  \
                                            ADSi);                                                                 \
     }
@@ -254,60 +367,72 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
     ODWF_HOP_DIR(2, 0); ODWF_HOP_DIR(2, 1);
     ODWF_HOP_DIR(3, 0); ODWF_HOP_DIR(3, 1);
 #undef ODWF_HOP_DIR
-    float acc[24];
+    // y = W psi (or W^dag psi) in pairs; the lower half gathers AD and the swapped ADS
+    Half6 up, dn;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        acc[2 * c] = AUr[c].x;
-        acc[2 * c + 1] = AUi[c].x;
-        acc[6 + 2 * c] = AUr[c].y;
-        acc[6 + 2 * c + 1] = AUi[c].y;
-        acc[12 + 2 * c] = ADr[c].x + ADSr[c].y;
-        acc[12 + 2 * c + 1] = ADi[c].x + ADSi[c].y;
-        acc[18 + 2 * c] = ADr[c].y + ADSr[c].x;
-        acc[18 + 2 * c + 1] = ADi[c].y + ADSi[c].x;
+        up.R[c] = AUr[c];
+        up.I[c] = AUi[c];
+        dn.R[c] = __fadd2_rn(ADr[c], make_float2(ADSr[c].y, ADSr[c].x));
+        dn.I[c] = __fadd2_rn(ADi[c], make_float2(ADSi[c].y, ADSi[c].x));
     }
 
     const Coef5<float>& cf = P.cf;
     float nrm = 0.f;  // per-thread partial sums in FP32, FP64 across warps and blocks (block_sum)
+    float v[24];
     if (KIND == K1) {
         // chi_t = B M^-1 (-1/2 y)
-        minv_apply_f<false>(acc, cf, r, s, NS, false, -0.5f);
-        bidiag_apply(acc, cf.rho[s], cf.sigma[s], r, s, NS, false);
-        if (valid) SpinorIO<SP, float>::store(P.out.d(sys), P.out.n(sys), (size_t)h, s, NS, acc);
+        minv_pairs<NS>(up, dn, cf, r, s, false, -0.5f);
+        bidiag_pairs<NS>(up, dn, cf.rho[s], cf.sigma[s], r, s, false);
+        pairs_to_mem(up, dn, v);
+        if (valid) SpinorIO<SP, float>::store(P.out.d(sys), P.out.n(sys), (size_t)h, s, NS, v);
     } else if (KIND == K2) {
         // s = p - M^-1 (-1/2 y) = p + M^-1 (y/2);  |s|^2;  a = M^-dag s
-        minv_apply_f(acc, cf, r, s, NS, false, 0.5f);
-        float z[24];
+        minv_pairs<NS>(up, dn, cf, r, s, false, 0.5f);
         if (valid) {
-            SpinorIO<SP, float>::load(P.z.d(sys), P.z.n(sys), (size_t)h, s, NS, z);
+            SpinorIO<SP, float>::load(P.z.d(sys), P.z.n(sys), (size_t)h, s, NS, v);
         } else {
 #pragma unroll
-            for (int k = 0; k < 24; ++k) z[k] = 0.f;
+            for (int k = 0; k < 24; ++k) v[k] = 0.f;
         }
+        Half6 zu, zd;
+        mem_to_pairs(v, zu, zd);
+        float2 n2 = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < 24; ++k) {
-            acc[k] += z[k];
-            nrm = fmaf(acc[k], acc[k], nrm);
+        for (int k = 0; k < 6; ++k) {
+            up.p(k) = __fadd2_rn(up.p(k), zu.p(k));
+            dn.p(k) = __fadd2_rn(dn.p(k), zd.p(k));
+            n2 = fma2(up.p(k), up.p(k), n2);
+            n2 = fma2(dn.p(k), dn.p(k), n2);
         }
-        if (!valid) nrm = 0.f;  // a site past the end computed site 0's neighbours: no contribution
-        minv_apply_f(acc, cf, r, s, NS, true, 1.f);
-        if (valid) SpinorIO<SP, float>::store(P.out.d(sys), P.out.n(sys), (size_t)h, s, NS, acc);
+        nrm = valid ? n2.x + n2.y : 0.f;  // a site past the end computed site 0's neighbours: no contribution
+        minv_pairs<NS>(up, dn, cf, r, s, true, 1.f);
+        pairs_to_mem(up, dn, v);
+        if (valid) SpinorIO<SP, float>::store(P.out.d(sys), P.out.n(sys), (size_t)h, s, NS, v);
     } else if (KIND == K3) {
         // c = M^-dag (-1/2 B^dag y)
-        bidiag_apply(acc, cf.rho[s], cf.sigma[s], r, s, NS, true);
-        minv_apply_f(acc, cf, r, s, NS, true, -0.5f);
-        if (valid) SpinorIO<SP, float>::store(P.out.d(sys), P.out.n(sys), (size_t)h, s, NS, acc);
+        bidiag_pairs<NS>(up, dn, cf.rho[s], cf.sigma[s], r, s, true);
+        minv_pairs<NS>(up, dn, cf, r, s, true, -0.5f);
+        pairs_to_mem(up, dn, v);
+        if (valid) SpinorIO<SP, float>::store(P.out.d(sys), P.out.n(sys), (size_t)h, s, NS, v);
     } else {
         // A p = M^dag a + 1/2 B^dag y;  r -= alpha A p;  x += alpha p
-        bidiag_apply(acc, cf.rho[s], cf.sigma[s], r, s, NS, true);
-        float z[24];
+        bidiag_pairs<NS>(up, dn, cf.rho[s], cf.sigma[s], r, s, true);
         if (valid) {
-            SpinorIO<SP, float>::load(P.z.d(sys), P.z.n(sys), (size_t)h, s, NS, z);
+            SpinorIO<SP, float>::load(P.z.d(sys), P.z.n(sys), (size_t)h, s, NS, v);
         } else {
 #pragma unroll
-            for (int k = 0; k < 24; ++k) z[k] = 0.f;
+            for (int k = 0; k < 24; ++k) v[k] = 0.f;
         }
-        bidiag_apply(z, cf.d[s], cf.e[s], r, s, NS, true);
+        Half6 zu, zd;
+        mem_to_pairs(v, zu, zd);
+        bidiag_pairs<NS>(zu, zd, cf.d[s], cf.e[s], r, s, true);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            up.p(k) = fma2(f2(0.5f), up.p(k), zu.p(k));
+            dn.p(k) = fma2(f2(0.5f), dn.p(k), zd.p(k));
+        }
+        pairs_to_mem(up, dn, v);  // v = A p
         const float alpha = (float)P.st[sys].alpha;
         if (valid) {
             float rv[24], xv[24], pv[24];
@@ -316,8 +441,7 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
             SpinorIO<SP, float>::load(P.cg_p.d(sys), P.cg_p.n(sys), (size_t)h, s, NS, pv);
 #pragma unroll
             for (int k = 0; k < 24; ++k) {
-                const float ap = fmaf(0.5f, acc[k], z[k]);
-                rv[k] = fmaf(-alpha, ap, rv[k]);
+                rv[k] = fmaf(-alpha, v[k], rv[k]);
                 xv[k] = fmaf(alpha, pv[k], xv[k]);
                 nrm = fmaf(rv[k], rv[k], nrm);
             }
@@ -388,7 +512,12 @@ cudaError_t hop2_ns(const HopParams<float>& P, int kind, int nsys, cudaStream_t 
 
 template <class SP>
 cudaError_t hop2_lk(const HopParams<float>& P, int kind, Lk lk, int nsys, cudaStream_t st) {
-    return lk == Lk::F12 ? hop2_ns<SP, LinkF12>(P, kind, nsys, st) : hop2_ns<SP, LinkF18>(P, kind, nsys, st);
+    switch (lk) {
+        case Lk::F12: return hop2_ns<SP, LinkF12>(P, kind, nsys, st);
+        case Lk::F18: return hop2_ns<SP, LinkF18>(P, kind, nsys, st);
+        case Lk::H12: return hop2_ns<SP, LinkH12>(P, kind, nsys, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <class SP, int NS>

@@ -168,11 +168,14 @@ struct SpinorIO<SpBF16, R> : HalfIO<__nv_bfloat162, R> {};
 
 // Link field: for each parity p, direction mu and half-site h, U_mu(x) of site (p, h),
 // row-major 3x3 complex.  LinkD18: 18 doubles; LinkF18: 18 floats padded to 20;
-// LinkF12: rows 0 and 1 as 12 floats, row 2 = conj(row0 x row1) rebuilt in registers.
+// LinkF12: rows 0 and 1 as 12 floats, row 2 = conj(row0 x row1) rebuilt in registers;
+// LinkH12: rows 0 and 1 as 12 FP16 values (no scale: every entry of an SU(3) matrix has
+// modulus <= 1, inside FP16's normal range), row 2 rebuilt in FP32.
 // Address: ((p * 4 + mu) * Vh + h) * BYTES.
 struct LinkD18 { static constexpr int BYTES = 144; };
 struct LinkF18 { static constexpr int BYTES = 80; };
 struct LinkF12 { static constexpr int BYTES = 48; };
+struct LinkH12 { static constexpr int BYTES = 24; };
 
 template <class LK, class R>
 struct LinkIO;
@@ -225,6 +228,39 @@ struct LinkIO<LinkF12, R> {
             u[12 + 2 * j] = re;
             u[12 + 2 * j + 1] = -im;
         }
+    }
+};
+
+// row2[j] = conj(row0[j+1] row1[j+2] - row0[j+2] row1[j+1]) (indices mod 3): the third row of
+// an SU(3) matrix from its first two (u[0..11] = rows 0, 1; fills u[12..17])
+template <class R>
+__device__ __forceinline__ void su3_third_row(R u[18]) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int a = (j + 1) % 3, b = (j + 2) % 3;
+        const R ar = u[2 * a], ai = u[2 * a + 1], br = u[2 * b], bi = u[2 * b + 1];
+        const R cr = u[6 + 2 * a], ci = u[6 + 2 * a + 1], dr = u[6 + 2 * b], di = u[6 + 2 * b + 1];
+        const R re = (ar * dr - ai * di) - (br * cr - bi * ci);
+        const R im = (ar * di + ai * dr) - (br * ci + bi * cr);
+        u[12 + 2 * j] = re;
+        u[12 + 2 * j + 1] = -im;
+    }
+}
+
+template <class R>
+struct LinkIO<LinkH12, R> {
+    static __device__ __forceinline__ void load(const void* base, size_t idx, R u[18]) {
+        const uint2* p = reinterpret_cast<const uint2*>(reinterpret_cast<const char*>(base) + idx * 24);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint2 q = __ldg(p + k);
+            __half2 a, b;
+            *reinterpret_cast<uint32_t*>(&a) = q.x;
+            *reinterpret_cast<uint32_t*>(&b) = q.y;
+            const float2 fa = __half22float2(a), fb = __half22float2(b);
+            u[4 * k] = (R)fa.x; u[4 * k + 1] = (R)fa.y; u[4 * k + 2] = (R)fb.x; u[4 * k + 3] = (R)fb.y;
+        }
+        su3_third_row(u);
     }
 };
 

@@ -16,6 +16,11 @@
 //   3. drop idle groups to return their memory to the budget.
 // New requests therefore enter running batches between iterations, as slots and
 // memory free up.  Caller buffers must stay valid until the ticket completes.
+// A second thread copies finished solutions out to host buffers, so the worker never waits
+// for a device-to-host copy.  Any CUDA or solver error in a group fails every request that
+// has systems in it (with that status) and drops the group.  Requests can be cancelled, and a
+// policy can shed requests that waited too long for admission or refuse new ones when the
+// queue is full (serve_set_policy).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -55,6 +60,7 @@ struct Request {
     double latency_ms = 0, queue_ms = 0;
     bool admitted = false;
     bool done = false;
+    bool cancel = false;  // serve_cancel of a running request: its slots stop between chunks
 };
 
 struct Group {
@@ -67,8 +73,11 @@ struct Group {
     cudaEvent_t ev_chunk = nullptr;  // end of the last launched chunk of iterations
     bool in_flight = false;
     size_t reserved = 0;
-    std::vector<std::shared_ptr<Request>> slot_req;  // owner of each slot
+    std::vector<std::shared_ptr<Request>> slot_req;  // owner of each slot (until its copy-out is done)
     std::vector<int> slot_rhs;
+    std::vector<cudaEvent_t> ev_out;  // per slot: its solution has been unpacked into the staging buffer
+    bool failed = false;              // an error: requests failed, the group is dropped
+    int copies = 0;                   // copy-out jobs of this group queued or running
     Clock::time_point last_used;
     int used_slots() const {
         int n = 0;
@@ -92,7 +101,27 @@ struct serve_handle {
     std::map<uint64_t, std::shared_ptr<odwf::Request>> tickets;
     std::vector<std::unique_ptr<odwf::Group>> groups;
     std::thread worker;
-    std::string worker_error;
+    // copy-out of finished systems whose x is host memory (one job per system)
+    struct CopyJob {
+        odwf::Group* g;
+        int slot;
+        std::shared_ptr<odwf::Request> R;
+        void* dst;
+        const void* src;
+        size_t bytes;
+        int code;
+        int iters;
+        double resid;
+    };
+    std::deque<CopyJob> copy_jobs;
+    std::condition_variable cv_copy;
+    std::thread copier;
+    bool copier_stop = false;
+    // policy: requests still queued after admit_deadline_ms are shed (ODWF_ETIMEOUT); at most
+    // max_queued requests wait (serve_submit answers ODWF_EBUSY beyond); <= 0 disables each
+    double admit_deadline_ms = 0;
+    int max_queued = 0;
+    uint64_t shed = 0, refused = 0;
 };
 
 namespace odwf {
@@ -103,14 +132,16 @@ constexpr int kMaxSlots = 16;
 constexpr int kIterChunk = 8;
 
 size_t per_system_bytes(size_t sites5, int prec) {
-    if (prec == ODWF_F64) return sites5 * 192 * 7;
+    // x staging for a host output (external layout) and a device copy of a host b
+    if (prec == ODWF_F64) return sites5 * 192 * 8;
     const size_t lowb = prec == ODWF_F32 ? 96 : 52;
-    // FP64 x, a device copy of a host b, FP32 r and x, five low-precision fields
-    return sites5 * (192 * 2 + 96 * 2 + lowb * 5);
+    // FP64 x, a device copy of a host b, x staging, FP32 r and x, five low-precision fields
+    return sites5 * (192 * 3 + 96 * 2 + lowb * 5);
 }
 
 size_t group_fixed_bytes(size_t vh, size_t sites5) {
-    return 8 * vh * (144 + 80 + 48) + sites5 * 192 * 6 + (1 << 20);  // links, FP64 temporaries, scratch
+    // links (FP64, FP32-18, FP32-12 and its site-major copy), FP64 temporaries, scratch
+    return 8 * vh * (144 + 80 + 48 + 96) + sites5 * 192 * 6 + (1 << 20);
 }
 
 std::string group_key(const odwf_request& r, const std::vector<double>& om) {
@@ -193,6 +224,8 @@ bool try_admit(serve_handle* S, const std::shared_ptr<Request>& R, std::unique_l
         S->used += g->reserved;
         g->slot_req.assign(cap, nullptr);
         g->slot_rhs.assign(cap, -1);
+        g->ev_out.assign(cap, nullptr);
+        for (auto& e : g->ev_out) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
         G = g.get();
         S->groups.push_back(std::move(g));
     }
@@ -223,9 +256,61 @@ bool try_admit(serve_handle* S, const std::shared_ptr<Request>& R, std::unique_l
     return true;
 }
 
-// Hand the group's finished systems back: copy x out, free the slot, complete requests
-// whose systems are all done.  Called from the worker with the serve lock released.
-void harvest(serve_handle* S, Group* g) {
+void destroy_group(Group* g) {
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    g->cg.reset();
+    g->eng.reset();
+    for (auto& e : g->ev_out)
+        if (e) cudaEventDestroy(e);
+    g->ev_out.clear();
+    if (g->ev_chunk) cudaEventDestroy(g->ev_chunk);
+    if (g->stream) cudaStreamDestroy(g->stream);
+    g->ev_chunk = nullptr;
+    g->stream = nullptr;
+}
+
+// One system of R finished with `code`: count it, complete R when it was the last.
+void system_done(serve_handle* S, const std::shared_ptr<Request>& R, int code, int iters, double resid) {
+    R->iters = std::max(R->iters, iters);
+    R->resid = std::max(R->resid, resid);
+    if (code && R->status == ODWF_PENDING) R->status = code;
+    if (--R->remaining == 0 && !R->done) complete(S, R, R->status == ODWF_PENDING ? ODWF_OK : R->status);
+}
+
+// An error in group g: fail every request with systems in it and mark the group for dropping.
+// Called with the serve lock held.
+void fail_group(serve_handle* S, Group* g, int code) {
+    g->failed = true;
+    for (size_t i = 0; i < g->slot_req.size(); ++i) {
+        auto R = g->slot_req[i];
+        if (R && !R->done) complete(S, R, code);
+    }
+}
+
+// Cancelled requests give up their slots (between chunks; no copy-out).  Lock released.
+int drop_cancelled(serve_handle* S, Group* g) {
+    BatchCG& cg = *g->cg;
+    for (int i = 0; i < cg.cap; ++i) {
+        std::shared_ptr<Request> R;
+        {
+            std::lock_guard<std::mutex> g2(S->mu);
+            R = g->slot_req[i];
+            if (!R || !R->cancel || !cg.active[i]) continue;
+        }
+        const int rc = cg.cancel(i, g->stream);
+        if (rc) return rc;
+        std::lock_guard<std::mutex> g2(S->mu);
+        g->slot_req[i] = nullptr;
+        g->slot_rhs[i] = -1;
+        if (!R->done) complete(S, R, ODWF_ECANCELED);
+    }
+    return ODWF_OK;
+}
+
+// Hand the group's finished systems back: x into the caller's device buffer (stream-ordered),
+// or into a per-slot staging buffer whose copy to the caller's host buffer the copier thread
+// does; free the slot, complete requests whose systems are all done.  Lock released.
+int harvest(serve_handle* S, Group* g) {
     BatchCG& cg = *g->cg;
     for (int i = 0; i < cg.cap; ++i) {
         if (!cg.active[i] || !cg.slot_finished(i)) continue;
@@ -244,28 +329,53 @@ void harvest(serve_handle* S, Group* g) {
         int rc = ODWF_OK;
         double2* dx = (double2*)xo;
         const bool host = !is_device_ptr(xo);
-        if (host) dx = (double2*)g->eng->get_ws("serve.x", eb, &rc);
+        if (host) dx = (double2*)g->eng->get_ws("serve.x" + std::to_string(i), eb, &rc);
         double tr = 0;
-        if (!rc) rc = cg.finalize(i, dx, g->stream, &tr);
-        if (!rc && host) {
-            if (cudaMemcpyAsync(xo, dx, eb, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
-                cudaStreamSynchronize(g->stream) != cudaSuccess)
-                rc = ODWF_ECUDA;
-        }
+        if (!rc) rc = cg.finalize(i, dx, g->stream, &tr);  // synchronizes the group's stream
+        if (rc) return rc;
         const int stt = cg.st_host[i].status;
         const int iters = cg.st_host[i].iter;
         cg.release(i);
+        int code = ODWF_OK;
+        if (stt == kBreakdown) code = ODWF_EBREAKDOWN;
+        else if (stt != kDone) code = ODWF_ENOCONV;
         std::lock_guard<std::mutex> g2(S->mu);
-        g->slot_req[i] = nullptr;
-        g->slot_rhs[i] = -1;
-        R->iters = std::max(R->iters, iters);
-        R->resid = std::max(R->resid, tr);
-        int code = rc;
-        if (!code && stt == kBreakdown) code = ODWF_EBREAKDOWN;
-        if (!code && stt != kDone) code = ODWF_ENOCONV;
-        if (code && R->status == ODWF_PENDING) R->status = code;
-        if (--R->remaining == 0) complete(S, R, R->status == ODWF_PENDING ? ODWF_OK : R->status);
+        if (host && !R->done) {
+            // the slot stays owned by R until the copier has read the staging buffer
+            S->copy_jobs.push_back({g, i, R, xo, dx, eb, code, iters, tr});
+            ++g->copies;
+            S->cv_copy.notify_all();
+        } else {
+            g->slot_req[i] = nullptr;
+            g->slot_rhs[i] = -1;
+            if (!R->done) system_done(S, R, code, iters, tr);
+        }
         g->last_used = Clock::now();
+    }
+    return ODWF_OK;
+}
+
+// Copier thread: blocking device-to-host copies of finished solutions, off the worker.
+void copier_loop(serve_handle* S) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (true) {
+        S->cv_copy.wait(lk, [&] { return S->copier_stop || !S->copy_jobs.empty(); });
+        if (S->copy_jobs.empty() && S->copier_stop) break;
+        serve_handle::CopyJob j = S->copy_jobs.front();
+        S->copy_jobs.pop_front();
+        lk.unlock();
+        int rc = ODWF_OK;
+        if (cudaMemcpy(j.dst, j.src, j.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            rc = ODWF_ECUDA;
+        }
+        lk.lock();
+        --j.g->copies;
+        j.g->slot_req[j.slot] = nullptr;
+        j.g->slot_rhs[j.slot] = -1;
+        if (!j.R->done) system_done(S, j.R, rc ? rc : j.code, j.iters, j.resid);
+        S->cv_work.notify_all();
     }
 }
 
@@ -277,28 +387,60 @@ void worker_loop(serve_handle* S) {
         //    for other groups may still enter).  try_admit drops the lock around device work,
         //    so iterate over a snapshot of the queue.
         std::vector<std::shared_ptr<Request>> snap(S->queue.begin(), S->queue.end());
+        const auto now = Clock::now();
         for (auto& R : snap) {
             if (S->stop) break;
+            const double waited = std::chrono::duration<double, std::milli>(now - R->t_submit).count();
+            if (R->cancel || (S->admit_deadline_ms > 0 && waited > S->admit_deadline_ms)) {
+                // cancelled while queued, or shed: waited longer than the admission deadline
+                if (!R->cancel) ++S->shed;
+                complete(S, R, R->cancel ? ODWF_ECANCELED : ODWF_ETIMEOUT);
+                auto it = std::find(S->queue.begin(), S->queue.end(), R);
+                if (it != S->queue.end()) S->queue.erase(it);
+                continue;
+            }
             if (try_admit(S, R, lk)) {
                 auto it = std::find(S->queue.begin(), S->queue.end(), R);
                 if (it != S->queue.end()) S->queue.erase(it);
             }
         }
+        // drop failed groups (their requests were failed; pending copy-outs of the group are
+        // abandoned first so that nothing refers to it)
+        for (auto it = S->groups.begin(); it != S->groups.end();) {
+            Group* g = it->get();
+            if (!g->failed) {
+                ++it;
+                continue;
+            }
+            for (auto jt = S->copy_jobs.begin(); jt != S->copy_jobs.end();) {
+                if (jt->g == g) {
+                    --g->copies;
+                    jt = S->copy_jobs.erase(jt);
+                } else {
+                    ++jt;
+                }
+            }
+            if (g->copies > 0) {  // a copy the copier has taken: drop the group once it is done
+                ++it;
+                continue;
+            }
+            lk.unlock();
+            destroy_group(g);
+            lk.lock();
+            S->used -= std::min(S->used, g->reserved);
+            it = S->groups.erase(it);
+        }
         bool any = false;
         for (auto& g : S->groups)
             if (g->cg && g->cg->any_running()) any = true;
-        if (S->stop && !any) break;
+        if (S->stop && !any && S->copy_jobs.empty()) break;
         if (!any) {
             // 3. drop idle groups (their memory goes back to the budget), then sleep
             for (auto it = S->groups.begin(); it != S->groups.end();) {
                 Group* g = it->get();
                 if (g->used_slots() == 0) {
                     lk.unlock();
-                    if (g->stream) cudaStreamSynchronize(g->stream);
-                    g->cg.reset();
-                    g->eng.reset();
-                    if (g->ev_chunk) cudaEventDestroy(g->ev_chunk);
-                    if (g->stream) cudaStreamDestroy(g->stream);
+                    destroy_group(g);
                     lk.lock();
                     S->used -= std::min(S->used, g->reserved);
                     it = S->groups.erase(it);
@@ -318,35 +460,49 @@ void worker_loop(serve_handle* S) {
         bool launched = false;
         for (Group* g : act) {
             BatchCG& cg = *g->cg;
+            int rc = ODWF_OK;
             if (g->in_flight) {
                 const cudaError_t q = cudaEventQuery(g->ev_chunk);
                 if (q == cudaErrorNotReady) continue;
                 g->in_flight = false;
-                if (cg.poll(g->stream)) continue;
-                cg.service(g->stream);
-                harvest(S, g);
+                if (q != cudaSuccess) rc = cuda_fail(q, "serve: iteration chunk");
+                if (!rc) rc = cg.poll(g->stream);
+                if (!rc) rc = cg.service(g->stream);
+                if (!rc) rc = harvest(S, g);
+                if (!rc) rc = drop_cancelled(S, g);
             }
-            if (!cg.any_running()) continue;
-            cg.resume(g->stream, false);
-            cg.run_iterations(kIterChunk, g->stream);
-            if (cudaEventRecord(g->ev_chunk, g->stream) == cudaSuccess) g->in_flight = true;
-            launched = true;
+            if (!rc && cg.any_running()) {
+                rc = cg.resume(g->stream, false);
+                if (!rc) rc = cg.run_iterations(kIterChunk, g->stream);
+                if (!rc) {
+                    const cudaError_t e = cudaEventRecord(g->ev_chunk, g->stream);
+                    if (e != cudaSuccess) rc = cuda_fail(e, "serve: cudaEventRecord");
+                    else g->in_flight = true;
+                }
+                launched = true;
+            }
+            if (rc) {
+                std::lock_guard<std::mutex> g2(S->mu);
+                fail_group(S, g, rc);
+            }
         }
         if (!launched) std::this_thread::sleep_for(std::chrono::microseconds(100));
         lk.lock();
     }
-    // fail whatever is still queued
+    // fail whatever is still queued, let the copier finish the groups' copy-outs, free the groups
     for (auto& R : S->queue) complete(S, R, ODWF_ETIMEOUT);
     S->queue.clear();
-    lk.unlock();
-    for (auto& g : S->groups) {
-        if (g->stream) cudaStreamSynchronize(g->stream);
-        g->cg.reset();
-        g->eng.reset();
-        if (g->ev_chunk) cudaEventDestroy(g->ev_chunk);
-        if (g->stream) cudaStreamDestroy(g->stream);
+    while (true) {
+        int copies = 0;
+        for (auto& g : S->groups) copies += g->copies;
+        if (!copies) break;
+        S->cv_work.wait_for(lk, std::chrono::milliseconds(10));
     }
+    lk.unlock();
+    for (auto& g : S->groups) destroy_group(g.get());
+    lk.lock();
     S->groups.clear();
+    lk.unlock();
 }
 
 }  // namespace
@@ -369,6 +525,7 @@ int serve_create(size_t hbm_budget_bytes, serve_handle** out) {
         S->device = dev;
         S->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
         S->worker = std::thread(odwf::worker_loop, S);
+        S->copier = std::thread(odwf::copier_loop, S);
         *out = S;
         return ODWF_OK;
     } catch (...) {
@@ -425,6 +582,10 @@ int serve_submit(serve_handle* S, const odwf_request* req, uint64_t* ticket) {
     size_t field_bytes = 0;
     for (auto& kv : S->fields) field_bytes += kv.second.bytes;
     if (need + field_bytes > S->budget) return fail(ODWF_ENOMEM, "serve_submit: request can never fit the HBM budget");
+    if (S->max_queued > 0 && (int)S->queue.size() >= S->max_queued) {
+        ++S->refused;
+        return fail(ODWF_EBUSY, "serve_submit: the queue is full (serve_set_policy max_queued)");
+    }
     R->ticket = S->next_ticket++;
     S->tickets[R->ticket] = R;
     S->queue.push_back(R);
@@ -452,6 +613,33 @@ int serve_poll(serve_handle* S, uint64_t ticket, int timeout_ms, odwf_result* re
     return R->done ? R->status : ODWF_PENDING;
 }
 
+int serve_set_policy(serve_handle* S, double admit_deadline_ms, int max_queued) {
+    if (!S) return fail(ODWF_EINVAL, "serve_set_policy: null handle");
+    if (!std::isfinite(admit_deadline_ms)) return fail(ODWF_EINVAL, "serve_set_policy: non-finite deadline");
+    std::lock_guard<std::mutex> g(S->mu);
+    S->admit_deadline_ms = admit_deadline_ms;
+    S->max_queued = max_queued;
+    S->cv_work.notify_all();
+    return ODWF_OK;
+}
+
+int serve_cancel(serve_handle* S, uint64_t ticket) {
+    if (!S) return fail(ODWF_EINVAL, "serve_cancel: null handle");
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) return fail(ODWF_ENOTFOUND, "serve_cancel: unknown ticket");
+    auto& R = it->second;
+    if (R->done) return ODWF_OK;  // already finished: its status stands
+    R->cancel = true;
+    if (!R->admitted) {
+        auto q = std::find(S->queue.begin(), S->queue.end(), R);
+        if (q != S->queue.end()) S->queue.erase(q);
+        odwf::complete(S, R, ODWF_ECANCELED);
+    }
+    S->cv_work.notify_all();
+    return ODWF_OK;
+}
+
 int serve_destroy(serve_handle* S) {
     if (!S) return fail(ODWF_EINVAL, "serve_destroy: null handle");
     {
@@ -460,6 +648,12 @@ int serve_destroy(serve_handle* S) {
         S->cv_work.notify_all();
     }
     if (S->worker.joinable()) S->worker.join();
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->copier_stop = true;
+        S->cv_copy.notify_all();
+    }
+    if (S->copier.joinable()) S->copier.join();
     for (auto& kv : S->fields)
         if (kv.second.U) cudaFree(kv.second.U);
     delete S;
