@@ -483,6 +483,7 @@ def run_serve(args, world, rank, local):
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     srv = odwf.Server(0)
+    srv.set_policy(admit_deadline_ms=args.admit_deadline_ms, fair=args.fair)
     for k, dims in enumerate(SERVE_LATTICES):
         U = syn.gauge_field_torch(dims, EPS, 11 + k, device=dev)
         srv.register_gauge(k, dims, U)
@@ -511,34 +512,56 @@ def run_serve(args, world, rank, local):
             if rc != odwf._lib.ODWF_PENDING:
                 nrhs, k, ns = pending.pop(t)
                 done.append((res["latency_ms"], res["queue_ms"], rc, nrhs, k, ns, res["true_resid"]))
-                solves_done += nrhs
+                if rc == 0:
+                    solves_done += nrhs
         if now - t0 >= duration and (not pending or now - t0 >= duration + drain):
             break
         time.sleep(0.0005)
     wall = time.perf_counter() - t0
-    lat = np.array([d[0] for d in done]) if done else np.array([float("nan")])
-    bad = [d for d in done if d[2] != 0]
+    # every request that has ended: solved (status 0), shed at admission (ODWF_ETIMEOUT: waited
+    # past the deadline) or failed otherwise; latency = submit -> end
+    ok = [d for d in done if d[2] == 0]
+    shed = [d for d in done if d[2] == odwf._lib.ODWF_ETIMEOUT]
+    bad = [d for d in done if d[2] not in (0, odwf._lib.ODWF_ETIMEOUT)]
     codes = {}
     for d in bad:
         codes[str(d[2])] = codes.get(str(d[2]), 0) + 1
+
+    def pct(v, q):
+        return round(float(np.percentile(v, q)), 1) if len(v) else None
+
     per_lat = {}
     for d in done:
         key = "x".join(str(v) for v in SERVE_LATTICES[d[4]]) + "/Ns%d" % d[5]
-        e = per_lat.setdefault(key, {"completed": 0, "p50_ms": [], "solves": 0})
-        e["completed"] += 1
-        e["solves"] += d[3]
-        e["p50_ms"].append(d[0])
+        e = per_lat.setdefault(key, {"ended": 0, "solved": 0, "shed": 0, "solves": 0, "_ok": [], "_all": []})
+        e["ended"] += 1
+        e["_all"].append(d[0])
+        if d[2] == 0:
+            e["solved"] += 1
+            e["solves"] += d[3]
+            e["_ok"].append(d[0])
+        elif d[2] == odwf._lib.ODWF_ETIMEOUT:
+            e["shed"] += 1
     for e in per_lat.values():
-        e["p50_ms"] = round(float(np.percentile(e["p50_ms"], 50)), 1)
+        e["p50_solved_ms"], e["p99_solved_ms"] = pct(e["_ok"], 50), pct(e["_ok"], 99)
+        e["p50_all_ms"], e["p99_all_ms"] = pct(e["_all"], 50), pct(e["_all"], 99)
+        del e["_ok"], e["_all"]
+    lat_ok = [d[0] for d in ok]
+    lat_all = [d[0] for d in done]
     line = {"metric": "served ODWF D\u2020D solve latency (p50/p99) and throughput", "workload": "serve_poisson",
-            "rate_req_s": rate, "duration_s": duration, "submitted": submitted, "completed": len(done),
-            "pending_at_end": len(pending), "failed": len(bad), "failed_codes": codes, "per_lattice": per_lat,
+            "rate_req_s": rate, "duration_s": duration, "admit_deadline_ms": args.admit_deadline_ms,
+            "scheduling": "fair (equal stream priorities)" if args.fair else "smaller lattices first (stream priority)",
+            "submitted": submitted, "ended": len(done), "solved": len(ok), "shed_at_admission": len(shed),
+            "pending_at_end": len(pending), "failed": len(bad), "failed_codes": codes, "per_class": per_lat,
             "wall_s": round(wall, 2),
-            "p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2),
-            "throughput_req_s": round(len(done) / wall, 3), "throughput_solves_s": round(solves_done / wall, 3),
-            "max_true_resid": max([d[6] for d in done], default=None),
+            "p50_solved_ms": pct(lat_ok, 50), "p99_solved_ms": pct(lat_ok, 99),
+            "p50_all_ms": pct(lat_all, 50), "p99_all_ms": pct(lat_all, 99),
+            "throughput_req_s": round(len(ok) / wall, 3), "throughput_solves_s": round(solves_done / wall, 3),
+            "max_true_resid": max([d[6] for d in ok], default=None),
             "config": {"lattices": SERVE_LATTICES, "Ns": [8, 16], "mq": [0.002, 0.5], "nrhs": [1, 12],
-                       "prec": args.prec, "tol": TOL, "arrivals": "Poisson, seed 21"}}
+                       "prec": args.prec, "tol": TOL, "arrivals": "Poisson, seed 21",
+                       "shedding": "requests waiting longer than admit_deadline_ms for admission end with "
+                                   "ODWF_ETIMEOUT (their latency is submit -> shed)"}}
     print(json.dumps(line), flush=True)
     srv.close()
 
@@ -718,6 +741,36 @@ def run_profile_case(args, world, rank, local):
     h.close()
 
 
+def run_residual_mass(args, world, rank, local):
+    """Residual mass and pseudoscalar correlator of the effective 4D operator (Sec. 3, Table 1's
+    quantity) on a synthetic field: 16^4 x 16 (links exp(0.25 i H), seed 13), point source at
+    the origin, twelve effective solves per mass (FULL_DIRAC through the mixed-precision Schur
+    CG, tolerance 1e-10).  Reports m_res per mass, the solve time and iteration counts."""
+    import torch
+
+    import odwf_synth as syn
+    import paper_1811_08095_gb300 as odwf
+
+    torch.cuda.set_device(local)
+    dims = tuple(args.dims) if args.dims != list(DIMS) else (16, 16, 16, 16)
+    w, _ = odwf.odwf_zolotarev_omega(args.ns, LRANGE[0], LRANGE[1])
+    h = odwf.Handle(dims, args.ns, M0, 0.04, w)
+    h.set_gauge(syn.gauge_field_torch(dims, EPS, 13, device="cuda"))
+    out = []
+    for mq in (0.04, 0.5):
+        t = time.perf_counter()
+        mres, corr, st = h.residual_mass((0, 0, 0, 0), tol=TOL, prec=args.prec, mq=mq)
+        out.append({"mq": mq, "m_res": mres, "m_res_over_mq": mres / mq, "seconds": round(time.perf_counter() - t, 2),
+                    "inner_iters_12_solves": st["iters"], "worst_true_resid": st["true_resid"],
+                    "corr_t0_t1_tmid": [corr[0], corr[1], corr[len(corr) // 2]]})
+    h.close()
+    print(json.dumps({"workload": "residual_mass_%s_ns%d" % ("x".join(map(str, dims)), args.ns),
+                      "metric": "residual mass of the effective operator (point source, 12 solves per mass)",
+                      "prec": args.prec, "omega": "shifted (R5) Zolotarev on [0.05, 6.2]", "results": out,
+                      "reading": "m_res = tr G_00 / sum_x tr(G_x0^dag G_x0) - m_q, G = (D_eff^-1 - 1)/(2 m0 - m_q)"}),
+          flush=True)
+
+
 def run_reference(args, world, rank, local):
     """The oracle (FP64 CPU program) on host cores: each step is one oracle CG iteration on the
     workload, scaled to solves/s by the oracle's own iteration counts (tests/golden)."""
@@ -760,7 +813,7 @@ def main():
     ap.add_argument("--delta", type=float, default=0.01, help="reliable-update threshold")
     ap.add_argument("--link-recon", type=int, default=12, choices=[12, 18])
     ap.add_argument("--check-every", type=int, default=8, help="iterations between host polls of the solver state")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "serve", "profile"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "serve", "profile", "mres"],
                     help="c2: the default line; c3: 36-system batch on 24^3x48; c5: one 64^4 solve; serve; "
                          "profile: a fixed short solver run for ncu")
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS), help="profile: lattice")
@@ -770,6 +823,9 @@ def main():
     ap.add_argument("--rate", type=float, default=50.0, help="serve: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     ap.add_argument("--drain", type=float, default=60.0, help="serve: extra seconds to finish pending requests")
+    ap.add_argument("--admit-deadline-ms", type=float, default=10000.0,
+                    help="serve: requests not admitted within this time are shed (ODWF_ETIMEOUT); 0 = never")
+    ap.add_argument("--fair", action="store_true", help="serve: every batch at the same stream priority")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-dslash", action="store_true")
@@ -785,6 +841,8 @@ def main():
         run_paper_scale_c5(args, world, rank, local)
     elif args.workload == "profile":
         run_profile_case(args, world, rank, local)
+    elif args.workload == "mres":
+        run_residual_mass(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 

@@ -283,6 +283,33 @@ typedef struct {
 int odwf_mixed_cg_step(odwf_handle* h, int prec, int link_recon, int link_prec, double mq, const void* p_prev,
                        const void* r, const void* x, void* const* outs, odwf_cg_step_scalars* sc, void* stream);
 
+/*
+ * The 4D effective operator of Sec. 2 (the shifted-Zolotarev overlap that ODWF realizes):
+ *   x = D_eff(m_q)^-1 b,   D_eff(m_q) = (1 + r)/2 + (1 - r)/2 gamma_5 S(H_w),  r = m_q / (2 m0),
+ * computed through the 5D operator as [P^-1 D(m_q)^-1 D(2 m0) P (b (x) e_1)]_1 with
+ * P_{s,s'} = P_- delta_{s,s'} + P_+ delta_{s+1,s'} (s + 1 cyclic): D(2 m0) is applied in FP64 and
+ * D(m_q) y = eta is a FULL_DIRAC solve with `params` (prec, tol, max_iter, mq; system ignored).
+ * b, x: 4D fields psi[t][z][y][x][spin][colour] (V * 12 complex128, host or device, not
+ * overlapping).  Returns the D(m_q) solve's status; stats (may be NULL) describe that solve.
+ */
+int odwf_effective_solve(odwf_handle* h, void* x, const void* b, const odwf_solve_params* params,
+                         odwf_solve_stats* stats, void* stream);
+
+/*
+ * Residual mass of the effective operator at a point source (Sec. 3, Table 1's quantity).  The
+ * formula the paper uses is cited, not printed; the reading implemented is: with
+ * G = (D_c + m_q)^-1 = (D_eff^-1 - 1) / (2 m0 - m_q) the propagator of the chirally symmetric
+ * D_c = D (1 - D/(2 m0))^-1, D = (2 m0 D_eff - m_q) / (1 - m_q/(2 m0)),
+ *   m_res = tr G_00 / sum_x tr (G_x0^dag G_x0) - m_q,
+ * which vanishes for an exact sign function.  Twelve effective solves (one per spin-colour
+ * component of the source at `site` = {x, y, z, t}).  params as odwf_effective_solve (the mass
+ * is params->mq, NaN: the handle's).  *mres receives m_res; corr (Lt doubles, may be NULL)
+ * the pseudoscalar correlator C(t) = sum over the time slice t0 + t of tr (G_x0^dag G_x0).
+ * Returns the worst solve status (ODWF_OK when all converged).
+ */
+int odwf_residual_mass(odwf_handle* h, const int32_t* site, const odwf_solve_params* params, double* mres,
+                       double* corr, odwf_solve_stats* stats, void* stream);
+
 /* ----------------------------------------------------------------------------------
  * Kernel timing (no counterpart in the paper; used to place the kernels on the roofline).
  * ---------------------------------------------------------------------------------- */
@@ -370,12 +397,15 @@ int serve_submit(serve_handle* s, const odwf_request* req, uint64_t* ticket);
 int serve_poll(serve_handle* s, uint64_t ticket, int timeout_ms, odwf_result* res);
 
 /*
- * Admission policy.  admit_deadline_ms > 0: a request still waiting for admission after that
- * long is shed, completing with ODWF_ETIMEOUT (its x is not written).  max_queued > 0: at most
- * that many requests wait; serve_submit then answers ODWF_EBUSY and takes no ticket.  Values
- * <= 0 disable either (the default).  Applies to requests already queued from the next loop pass.
+ * Admission and scheduling policy.  admit_deadline_ms > 0: a request still waiting for admission
+ * after that long is shed, completing with ODWF_ETIMEOUT (its x is not written).  max_queued > 0:
+ * at most that many requests wait; serve_submit then answers ODWF_EBUSY and takes no ticket.
+ * Values <= 0 disable either (the default).  fair = 0 (default): batches of smaller lattices
+ * get higher stream priorities (short requests finish first); fair = 1: every batch created
+ * from now on runs at the same priority, so batches share the GPU in proportion to their work.
+ * Applies to requests already queued from the next loop pass.
  */
-int serve_set_policy(serve_handle* s, double admit_deadline_ms, int max_queued);
+int serve_set_policy(serve_handle* s, double admit_deadline_ms, int max_queued, int fair);
 
 /*
  * Cancel a request.  A queued request completes at once with ODWF_ECANCELED; a running one

@@ -99,3 +99,45 @@ def effective_zolotarev(U, ns, m0, mq, lmin, lmax, shifted=True, tbc=True):
     S = (vec * zolotarev.sign_approx(lam, ns, lmin, lmax, shifted)) @ vec.conj().T
     r = mq / (2.0 * m0)
     return 0.5 * (1 + r) * np.eye(12 * V) + 0.5 * (1 - r) * g5 @ S, lam
+
+
+def effective_dense(U, ns, m0, mq, lmin, lmax, shifted=True, tbc=True, exact_sign=False):
+    """D_eff(m_q) of Sec. 2 as a dense 4D matrix: (1 + r)/2 + (1 - r)/2 gamma_5 S(H_w) with
+    S the (shifted) Zolotarev sign approximation, or the exact sign function when exact_sign."""
+    if not exact_sign:
+        return effective_zolotarev(U, ns, m0, mq, lmin, lmax, shifted, tbc)[0]
+    lx, ly, lz, lt = _dims_of(U)
+    V = lx * ly * lz * lt
+    g5 = gamma5_4d(V)
+    Hw = g5 @ dense_dw(U, m0, tbc)
+    Hw = 0.5 * (Hw + Hw.conj().T)
+    lam, vec = np.linalg.eigh(Hw)
+    S = (vec * np.sign(lam)) @ vec.conj().T
+    r = mq / (2.0 * m0)
+    return 0.5 * (1 + r) * np.eye(12 * V) + 0.5 * (1 - r) * g5 @ S
+
+
+def effective_propagator(Deff, b4):
+    """x = D_eff^-1 b for a 4D field b of shape (Lt, Lz, Ly, Lx, 4, 3) (dense LU solve)."""
+    return np.linalg.solve(Deff, np.asarray(b4).reshape(-1)).reshape(np.shape(b4))
+
+
+def residual_mass(Deff, m0, mq, site_index):
+    """Residual mass read off the 4D effective operator at one source site.
+
+    With D(m_q) = 2 m0 D_eff = m_q + (1 - m_q/(2 m0)) D, the valence propagator of the chirally
+    symmetric operator D_c = D (1 - D/(2 m0))^-1 is G = (D_c + m_q)^-1 = (D_eff^-1 - 1)/(2 m0 - m_q).
+    m_res = tr G_00 / sum_x tr (G_x0^dag G_x0) - m_q (the second sum equals
+    tr [gamma_5 (D_c + m_q) gamma_5 (D_c + m_q)]^-1_00 by gamma_5-hermiticity); it vanishes when
+    S^2 = 1.  Returns (m_res, numerator, denominator, per_site) with per_site[x] =
+    tr (G_x0^dag G_x0) for every site x (lexicographic)."""
+    n = Deff.shape[0]
+    V = n // 12
+    cols = slice(12 * site_index, 12 * site_index + 12)
+    rhs = np.zeros((n, 12), dtype=np.complex128)
+    rhs[cols, :] = np.eye(12)
+    G = (np.linalg.solve(Deff, rhs) - rhs) / (2.0 * m0 - mq)  # columns G_{x0}, x over all sites
+    num = np.trace(G[cols, :]).real
+    per_site = (np.abs(G) ** 2).reshape(V, 12, 12).sum(axis=(1, 2))
+    den = per_site.sum()
+    return num / den - mq, num, den, per_site

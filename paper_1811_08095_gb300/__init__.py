@@ -162,6 +162,30 @@ class Handle:
                 "total_ms": out.total_ms, "bytes_per_system": out.bytes_per_system,
                 "bytes_per_launch": out.bytes_per_launch}
 
+    def effective_solve(self, x, b, tol=1e-10, max_iter=100000, prec="f64", mq=None, stream=None,
+                        raise_on_error=True, link_prec="f32"):
+        """odwf_effective_solve: x = D_eff(m_q)^-1 b on 4D fields (Lt, Lz, Ly, Lx, 4, 3)."""
+        p = _params(tol, max_iter, prec, 0.01, ODWF_SYS_FULL_DIRAC, 12, mq, 8, link_prec)
+        st = _lib.odwf_solve_stats()
+        rc = self._lib.odwf_effective_solve(self._h, ptr(x), ptr(b), ctypes.byref(p), ctypes.byref(st),
+                                            stream_ptr(stream))
+        if raise_on_error:
+            check(rc)
+        d = _stats_dict(st)
+        d["rc"] = rc
+        return d
+
+    def residual_mass(self, site, tol=1e-10, max_iter=100000, prec="f64", mq=None, stream=None):
+        """odwf_residual_mass at site (x, y, z, t): returns (m_res, C(t) array, stats dict)."""
+        p = _params(tol, max_iter, prec, 0.01, ODWF_SYS_FULL_DIRAC, 12, mq, 8)
+        st = _lib.odwf_solve_stats()
+        s4 = (ctypes.c_int32 * 4)(*[int(v) for v in site])
+        mres = ctypes.c_double(0.0)
+        corr = np.zeros(self.dims[3], dtype=np.float64)
+        check(self._lib.odwf_residual_mass(self._h, ctypes.cast(s4, ctypes.c_void_p), ctypes.byref(p),
+                                           ctypes.byref(mres), ptr(corr), ctypes.byref(st), stream_ptr(stream)))
+        return mres.value, corr, _stats_dict(st)
+
     def cg_solve(self, x, b, tol=1e-10, max_iter=100000, prec="f64", delta=0.01, system=ODWF_SYS_SCHUR_NORMAL,
                  link_recon=12, mq=None, check_every=8, stream=None, raise_on_error=True, link_prec="f32"):
         p = _params(tol, max_iter, prec, delta, system, link_recon, mq, check_every, link_prec)
@@ -233,8 +257,8 @@ class Server:
         self._keep[t.value] = (om, ba, xa, bs, xs)
         return t.value
 
-    def set_policy(self, admit_deadline_ms=0.0, max_queued=0):
-        check(self._lib.serve_set_policy(self._h, float(admit_deadline_ms), int(max_queued)))
+    def set_policy(self, admit_deadline_ms=0.0, max_queued=0, fair=False):
+        check(self._lib.serve_set_policy(self._h, float(admit_deadline_ms), int(max_queued), 1 if fair else 0))
 
     def cancel(self, ticket):
         check(self._lib.serve_cancel(self._h, ctypes.c_uint64(ticket)))

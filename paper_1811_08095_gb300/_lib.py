@@ -94,6 +94,8 @@ _SIGS = {
     "odwf_apply_m5_noalloc": ([I, D, D, P, P, P, ctypes.c_long, I, P], I),
     "odwf_mixed_cg_step": ([P, I, I, I, D, P, P, P, P, ctypes.POINTER(odwf_cg_step_scalars), P], I),
     "odwf_cg_solve": ([P, P, P, ctypes.POINTER(odwf_solve_params), P, P], I),
+    "odwf_effective_solve": ([P, P, P, ctypes.POINTER(odwf_solve_params), P, P], I),
+    "odwf_residual_mass": ([P, P, ctypes.POINTER(odwf_solve_params), ctypes.POINTER(D), P, P, P], I),
     "odwf_cg_solve_batched": ([P, I, P, P, P, ctypes.POINTER(odwf_solve_params), P, P], I),
     "odwf_profile_enable": ([I], I),
     "odwf_profile_read": ([P, I, ctypes.POINTER(ctypes.c_int)], I),
@@ -104,7 +106,7 @@ _SIGS = {
     "serve_submit": ([P, ctypes.POINTER(odwf_request), ctypes.POINTER(ctypes.c_uint64)], I),
     "serve_poll": ([P, ctypes.c_uint64, I, ctypes.POINTER(odwf_result)], I),
     "serve_destroy": ([P], I),
-    "serve_set_policy": ([P, D, I], I),
+    "serve_set_policy": ([P, D, I, I], I),
     "serve_cancel": ([P, ctypes.c_uint64], I),
 }
 

@@ -150,6 +150,28 @@ int odwf_time_kernel(odwf_handle* h, int kind, int prec, int link_recon, int lin
     GUARD_END
 }
 
+int odwf_effective_solve(odwf_handle* h, void* x, const void* b, const odwf_solve_params* params,
+                         odwf_solve_stats* stats, void* stream) {
+    GUARD_BEGIN
+    if (!h) return fail(ODWF_EINVAL, "odwf_effective_solve: null handle");
+    ON_DEVICE(h, "odwf_effective_solve", x, b);
+    const int rc = odwf::check_params(params);
+    if (rc) return rc;
+    return h->e.effective_solve(x, b, params, stats, (cudaStream_t)stream);
+    GUARD_END
+}
+
+int odwf_residual_mass(odwf_handle* h, const int32_t* site, const odwf_solve_params* params, double* mres,
+                       double* corr, odwf_solve_stats* stats, void* stream) {
+    GUARD_BEGIN
+    if (!h) return fail(ODWF_EINVAL, "odwf_residual_mass: null handle");
+    ON_DEVICE(h, "odwf_residual_mass");
+    const int rc = odwf::check_params(params);
+    if (rc) return rc;
+    return h->e.residual_mass(site, params, mres, corr, stats, (cudaStream_t)stream);
+    GUARD_END
+}
+
 int odwf_cg_solve(odwf_handle* h, void* x, const void* b, const odwf_solve_params* params, odwf_solve_stats* stats,
                   void* stream) {
     GUARD_BEGIN

@@ -492,7 +492,7 @@ int Engine::apply_m5(void* out, const void* in, long n_sites, int op, cudaStream
     return ODWF_OK;
 }
 
-static int check_params(const odwf_solve_params* prm) {
+int check_params(const odwf_solve_params* prm) {
     if (!prm) return fail(ODWF_EINVAL, "solve: null params");
     if (!(prm->tol > 0.0) || !std::isfinite(prm->tol)) return fail(ODWF_EINVAL, "solve: tol must be > 0");
     if (prm->max_iter <= 0) return fail(ODWF_EINVAL, "solve: max_iter must be > 0");

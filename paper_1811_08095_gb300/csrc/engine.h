@@ -27,6 +27,7 @@ bool is_device_ptr(const void* p);
 // ODWF_EINVAL when p is device memory of a GPU other than `dev` (kernels on `dev` cannot read it
 // without peer access); host, managed and unknown pointers pass.
 int check_ptr_device(const void* p, int dev, const char* what);
+int check_params(const odwf_solve_params* prm);  // ODWF_EINVAL with a message for bad solve parameters
 
 // A device buffer owned by the engine.
 struct DevBuf {
@@ -110,6 +111,10 @@ struct Engine {
     int apply_low_normal(void* out, const void* in, int prec, int recon, cudaStream_t st);
     int mixed_cg_step(int prec, int recon, int link_prec, double mq_step, const void* p_prev, const void* r, const void* x,
                       void* const* outs, odwf_cg_step_scalars* sc, cudaStream_t st);
+    int effective_solve(void* x, const void* b, const odwf_solve_params* prm, odwf_solve_stats* stats,
+                        cudaStream_t st);
+    int residual_mass(const int32_t site[4], const odwf_solve_params* prm, double* mres, double* corr,
+                      odwf_solve_stats* stats, cudaStream_t st);
     int time_kernel(int kind, int prec, int recon, int link_prec, int nsys, int reps, const void* fill,
                     odwf_kernel_prof* out, cudaStream_t st);
     int solve(int nsys, void* const* x, const void* const* b, const double* mq_arr, const odwf_solve_params* prm,

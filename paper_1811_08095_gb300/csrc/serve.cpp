@@ -22,6 +22,8 @@
 // policy can shed requests that waited too long for admission or refuse new ones when the
 // queue is full (serve_set_policy).
 #include <algorithm>
+#include <atomic>
+#include <cstdlib>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -121,6 +123,7 @@ struct serve_handle {
     // max_queued requests wait (serve_submit answers ODWF_EBUSY beyond); <= 0 disables each
     double admit_deadline_ms = 0;
     int max_queued = 0;
+    int fair = 0;  // 1: every batch at the same stream priority
     uint64_t shed = 0, refused = 0;
 };
 
@@ -130,6 +133,17 @@ namespace {
 
 constexpr int kMaxSlots = 16;
 constexpr int kIterChunk = 8;
+
+// Host-side failure injection for tests: with ODWF_SERVE_INJECT_ERROR=n in the environment the
+// n-th chunk launch of the process reports ODWF_ECUDA instead of launching (no device fault).
+long inject_at() {
+    static const long n = [] {
+        const char* v = std::getenv("ODWF_SERVE_INJECT_ERROR");
+        return v ? std::atol(v) : 0L;
+    }();
+    return n;
+}
+std::atomic<long> g_chunks{0};
 
 size_t per_system_bytes(size_t sites5, int prec) {
     // x staging for a host output (external layout) and a device copy of a host b
@@ -199,7 +213,8 @@ bool try_admit(serve_handle* S, const std::shared_ptr<Request>& R, std::unique_l
             int least = 0, greatest = 0;
             cudaDeviceGetStreamPriorityRange(&least, &greatest);
             int prio = greatest;
-            for (size_t w = sites5; w > (1u << 18) && prio < least; w >>= 2) ++prio;
+            if (!S->fair)
+                for (size_t w = sites5; w > (1u << 18) && prio < least; w >>= 2) ++prio;
             if (cudaStreamCreateWithPriority(&g->stream, cudaStreamNonBlocking, prio) != cudaSuccess ||
                 cudaEventCreateWithFlags(&g->ev_chunk, cudaEventDisableTiming) != cudaSuccess)
                 rc = ODWF_ECUDA;
@@ -472,7 +487,9 @@ void worker_loop(serve_handle* S) {
                 if (!rc) rc = drop_cancelled(S, g);
             }
             if (!rc && cg.any_running()) {
-                rc = cg.resume(g->stream, false);
+                if (inject_at() > 0 && ++g_chunks == inject_at())
+                    rc = fail(ODWF_ECUDA, "serve: injected failure of a chunk launch (ODWF_SERVE_INJECT_ERROR)");
+                if (!rc) rc = cg.resume(g->stream, false);
                 if (!rc) rc = cg.run_iterations(kIterChunk, g->stream);
                 if (!rc) {
                     const cudaError_t e = cudaEventRecord(g->ev_chunk, g->stream);
@@ -613,12 +630,13 @@ int serve_poll(serve_handle* S, uint64_t ticket, int timeout_ms, odwf_result* re
     return R->done ? R->status : ODWF_PENDING;
 }
 
-int serve_set_policy(serve_handle* S, double admit_deadline_ms, int max_queued) {
+int serve_set_policy(serve_handle* S, double admit_deadline_ms, int max_queued, int fair) {
     if (!S) return fail(ODWF_EINVAL, "serve_set_policy: null handle");
     if (!std::isfinite(admit_deadline_ms)) return fail(ODWF_EINVAL, "serve_set_policy: non-finite deadline");
     std::lock_guard<std::mutex> g(S->mu);
     S->admit_deadline_ms = admit_deadline_ms;
     S->max_queued = max_queued;
+    S->fair = fair ? 1 : 0;
     S->cv_work.notify_all();
     return ODWF_OK;
 }

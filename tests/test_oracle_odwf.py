@@ -239,3 +239,40 @@ def test_hop_w_composes_to_the_parity_blocks_of_d5(oracle_lib, tbc):
     got = oracle.b5(oracle.hop_w(U, po, 1, M0, tbc, dagger=True), M0, mq, w, dagger=True)
     ref = oracle.to_parity(oracle.d5(U, oracle.from_parity(po, dims, 1), M0, mq, w, tbc, dagger=True), dims, 0)
     assert np.abs(got - ref).max() < 1e-13
+
+
+def test_residual_mass_vanishes_for_exact_sign_and_shrinks_with_ns(oracle_lib, small):
+    """The residual-mass reading of the effective operator: exactly zero (to rounding) when the
+    sign function is exact (D_c then anticommutes with gamma_5), positive and O(d_Z) for the
+    shifted Zolotarev approximation, and smaller at larger N_s (smaller d_Z)."""
+    dims, U = small
+    mq = 0.05
+    ex = dense.effective_dense(U, 4, M0, mq, 0.05, 6.2, exact_sign=True)
+    m_ex, num, den, _ = dense.residual_mass(ex, M0, mq, 3)
+    assert abs(m_ex) < 1e-12 * abs(num / den)
+    res = {}
+    for ns in (4, 8):
+        d = dense.effective_dense(U, ns, M0, mq, 0.05, 6.2)
+        res[ns] = dense.residual_mass(d, M0, mq, 3)[0]
+    assert abs(res[8]) < abs(res[4])
+    _, dz4 = zolotarev.omega(4, 0.05, 6.2, True)
+    assert 0 < abs(res[4]) < 10 * dz4
+
+
+def test_effective_propagator_solves_the_effective_operator(oracle_lib, small):
+    """D_eff^-1 b from the dense 4D operator equals the 5D route [P^-1 D(m_q)^-1 D(m_PV) P (b x e_1)]_1
+    built from the dense 5D operators (the identity of Sec. 2 applied to a vector)."""
+    dims, U = small
+    ns, mq = 4, 0.1
+    w, _ = zolotarev.omega(ns, 0.05, 6.0, True)
+    Deff = dense.effective_dense(U, ns, M0, mq, 0.05, 6.0)
+    b4 = syn.gaussian_spinor(1, dims, 77)[0]
+    x = dense.effective_propagator(Deff, b4)
+    D = dense.dense_d5(U, ns, M0, mq, w)
+    Dpv = dense.dense_d5(U, ns, M0, 2 * M0, w)
+    V = 16
+    P = dense.chiral_perm(ns, V)
+    v5 = np.zeros(12 * ns * V, dtype=np.complex128)
+    v5[:12 * V] = b4.reshape(-1)
+    y = np.linalg.solve(P, np.linalg.solve(D, Dpv @ (P @ v5)))[:12 * V]
+    assert np.abs(y - x.reshape(-1)).max() < 1e-11 * np.abs(x).max()
