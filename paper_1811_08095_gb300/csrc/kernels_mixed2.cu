@@ -272,6 +272,85 @@ __device__ __forceinline__ void minv_pairs(Half6& up, Half6& dn, const Coef5<flo
     }
 }
 
+// Fields a kernel touches once per site (the CG vectors r, x, p and the z operand) are read and
+// written with the evict-first (streaming) cache policy, so that they do not push the neighbour
+// field, which each site's eight neighbours read again, out of L2.
+template <class SP, int NS>
+__device__ __forceinline__ void spinor_load_cs(const void* base, const float* norm, size_t h, int s, float v[24]) {
+    if (std::is_same<SP, SpF32>::value) {
+        const float4* p = reinterpret_cast<const float4*>(base);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 q = __ldcs(p + chunk_off(h, k, 6, NS, s));
+            v[4 * k] = q.x;
+            v[4 * k + 1] = q.y;
+            v[4 * k + 2] = q.z;
+            v[4 * k + 3] = q.w;
+        }
+    } else {
+        using H2 = typename std::conditional<std::is_same<SP, SpF16>::value, __half2, __nv_bfloat162>::type;
+        const uint4* p = reinterpret_cast<const uint4*>(base);
+        const float sc = __ldcs(norm + h * NS + s);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint4 q = __ldcs(p + chunk_off(h, k, 3, NS, s));
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                H2 hv;
+                *reinterpret_cast<uint32_t*>(&hv) = w[j];
+                const float2 f = Half2Cvt<H2>::to_f2(hv);
+                v[8 * k + 2 * j] = f.x * sc;
+                v[8 * k + 2 * j + 1] = f.y * sc;
+            }
+        }
+    }
+}
+
+// The site-major link array is also read exactly once per launch (the eight links of a site).
+template <class LK>
+__device__ __forceinline__ void link_load_cs(const void* base, size_t idx, float u[18]) {
+    if (std::is_same<LK, LinkF12>::value) {
+        const float4* p = reinterpret_cast<const float4*>(reinterpret_cast<const char*>(base) + idx * 48);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 q = __ldcs(p + k);
+            u[4 * k] = q.x; u[4 * k + 1] = q.y; u[4 * k + 2] = q.z; u[4 * k + 3] = q.w;
+        }
+        su3_third_row(u);
+    } else if (std::is_same<LK, LinkH12>::value) {
+        const uint2* p = reinterpret_cast<const uint2*>(reinterpret_cast<const char*>(base) + idx * 24);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint2 q = __ldcs(p + k);
+            __half2 a, b;
+            *reinterpret_cast<uint32_t*>(&a) = q.x;
+            *reinterpret_cast<uint32_t*>(&b) = q.y;
+            const float2 fa = __half22float2(a), fb = __half22float2(b);
+            u[4 * k] = fa.x; u[4 * k + 1] = fa.y; u[4 * k + 2] = fb.x; u[4 * k + 3] = fb.y;
+        }
+        su3_third_row(u);
+    } else {
+        const float4* p = reinterpret_cast<const float4*>(reinterpret_cast<const char*>(base) + idx * 80);
+        float t[20];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const float4 q = __ldcs(p + k);
+            t[4 * k] = q.x; t[4 * k + 1] = q.y; t[4 * k + 2] = q.z; t[4 * k + 3] = q.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 18; ++k) u[k] = t[k];
+    }
+}
+
+template <int NS>
+__device__ __forceinline__ void f32_store_cs(void* base, size_t h, int s, const float v[24]) {
+    float4* p = reinterpret_cast<float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        __stcs(p + chunk_off(h, k, 6, NS, s), make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
+}
+
 // memory order [spin][colour][re, im] <-> pairs
 __device__ __forceinline__ void pairs_to_mem(const Half6& up, const Half6& dn, float v[24]) {
 #pragma unroll
@@ -335,7 +414,7 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
     float* my_links = s_links + (threadIdx.x / NS) * kSL;
     if (s < 8) {
         float u[18];
-        LinkIO<LK, float>::load(P.links, ((size_t)p_out * P.g.Vh + h) * 8 + s, u);
+        link_load_cs<LK>(P.links, ((size_t)p_out * P.g.Vh + h) * 8 + s, u);
         float2* dst = reinterpret_cast<float2*>(my_links + s * kLS);
 #pragma unroll
         for (int k = 0; k < 9; ++k) dst[k] = make_float2(u[2 * k], u[2 * k + 1]);
@@ -390,7 +469,7 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
         // s = p - M^-1 (-1/2 y) = p + M^-1 (y/2);  |s|^2;  a = M^-dag s
         minv_pairs<NS>(up, dn, cf, r, s, false, 0.5f);
         if (valid) {
-            SpinorIO<SP, float>::load(P.z.d(sys), P.z.n(sys), (size_t)h, s, NS, v);
+            spinor_load_cs<SP, NS>(P.z.d(sys), P.z.n(sys), (size_t)h, s, v);
         } else {
 #pragma unroll
             for (int k = 0; k < 24; ++k) v[k] = 0.f;
@@ -419,7 +498,7 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
         // A p = M^dag a + 1/2 B^dag y;  r -= alpha A p;  x += alpha p
         bidiag_pairs<NS>(up, dn, cf.rho[s], cf.sigma[s], r, s, true);
         if (valid) {
-            SpinorIO<SP, float>::load(P.z.d(sys), P.z.n(sys), (size_t)h, s, NS, v);
+            spinor_load_cs<SP, NS>(P.z.d(sys), P.z.n(sys), (size_t)h, s, v);
         } else {
 #pragma unroll
             for (int k = 0; k < 24; ++k) v[k] = 0.f;
@@ -436,17 +515,17 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
         const float alpha = (float)P.st[sys].alpha;
         if (valid) {
             float rv[24], xv[24], pv[24];
-            SpinorIO<SpF32, float>::load(P.cg_r.d(sys), nullptr, (size_t)h, s, NS, rv);
-            SpinorIO<SpF32, float>::load(P.cg_x.d(sys), nullptr, (size_t)h, s, NS, xv);
-            SpinorIO<SP, float>::load(P.cg_p.d(sys), P.cg_p.n(sys), (size_t)h, s, NS, pv);
+            spinor_load_cs<SpF32, NS>(P.cg_r.d(sys), nullptr, (size_t)h, s, rv);
+            spinor_load_cs<SpF32, NS>(P.cg_x.d(sys), nullptr, (size_t)h, s, xv);
+            spinor_load_cs<SP, NS>(P.cg_p.d(sys), P.cg_p.n(sys), (size_t)h, s, pv);
 #pragma unroll
             for (int k = 0; k < 24; ++k) {
                 rv[k] = fmaf(-alpha, v[k], rv[k]);
                 xv[k] = fmaf(alpha, pv[k], xv[k]);
                 nrm = fmaf(rv[k], rv[k], nrm);
             }
-            SpinorIO<SpF32, float>::store(P.cg_r.d(sys), nullptr, (size_t)h, s, NS, rv);
-            SpinorIO<SpF32, float>::store(P.cg_x.d(sys), nullptr, (size_t)h, s, NS, xv);
+            f32_store_cs<NS>(P.cg_r.d(sys), (size_t)h, s, rv);
+            f32_store_cs<NS>(P.cg_x.d(sys), (size_t)h, s, xv);
         }
     }
     if (KIND == K2) reduce_and_finalize(nrm, P.partials, P.counters, P.st, sys, FIN_ALPHA);
