@@ -237,7 +237,7 @@ def dslash_roofline(args, dev, reps=20):
     g = torch.Generator(device=dev)
     g.manual_seed(1)
     fill = torch.randn((NS, vh, 4, 3), dtype=torch.complex128, device=dev, generator=g)
-    traffic = {}
+    traffic = {}  # (class, systems) -> DRAM bytes per launch from the committed ncu capture
     if os.path.exists(DSLASH_TRAFFIC):
         for line in open(DSLASH_TRAFFIC):
             parts = line.split()

@@ -147,6 +147,7 @@ int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStr
 
 int BatchCG::admit(int slot, const double2* b_ext, double mq_slot, cudaStream_t s, double tol_slot,
                    int max_iter_slot) {
+    NvtxRange nv_("odwf.cg.admit");
     if (slot < 0 || slot >= cap) return fail(ODWF_EINVAL, "admit: bad slot");
     mq[slot] = mq_slot;
     const size_t eb = E->sites5() * 12 * sizeof(double2);
@@ -244,6 +245,7 @@ int BatchCG::admit_internal(int slot, cudaStream_t s, double tol_slot, int max_i
 }
 
 int BatchCG::run_iterations(int k, cudaStream_t s) {
+    NvtxRange nv_("odwf.cg.iterations");
     int lo = cap, hi = -1;
     for (int i = 0; i < cap; ++i)
         if (active[i] && slot_running(i)) {
@@ -541,6 +543,7 @@ int BatchCG::fp64_residual(int slot, cudaStream_t s) {
 }
 
 int BatchCG::service(cudaStream_t s) {
+    NvtxRange nv_("odwf.cg.reliable_updates");
     const size_t n5 = E->sites5();
     for (int i = 0; i < cap; ++i) {
         if (!active[i] || upd[i] || st_host[i].status != kNeedUpdate) continue;
@@ -578,6 +581,7 @@ int BatchCG::service(cudaStream_t s) {
 }
 
 int BatchCG::finalize(int slot, double2* x_ext, cudaStream_t s, double* true_resid) {
+    NvtxRange nv_("odwf.cg.finalize");
     if (upd[slot]) {
         ODWF_CK(cudaStreamWaitEvent(s, ev_rel[slot], 0));
         upd[slot] = 0;

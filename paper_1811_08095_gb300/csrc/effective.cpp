@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "profile.h"
 
 namespace odwf {
 
@@ -39,6 +40,7 @@ cudaError_t spin_pair_copy(double2* dst, const double2* src, size_t V, int sp0, 
 int Engine::effective_solve(void* x, const void* b, const odwf_solve_params* prm, odwf_solve_stats* stats,
                             cudaStream_t st) {
     if (!gauge_set) return fail(ODWF_EINVAL, "odwf_effective_solve: gauge field not set");
+    NvtxRange nv_("odwf.effective_solve");
     if (!x || !b || !prm) return fail(ODWF_EINVAL, "odwf_effective_solve: null argument");
     const auto t0 = std::chrono::steady_clock::now();
     const size_t V = 2 * vh();

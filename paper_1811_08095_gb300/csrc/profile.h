@@ -8,6 +8,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <string>
 
@@ -26,5 +27,14 @@ int prof_class(const std::string& name, double bytes_per_system, double bytes_pe
 ProfSlot prof_begin(int cls, cudaStream_t s);
 void prof_end(const ProfSlot& slot, cudaStream_t s);
 void prof_collect();  // after a stream synchronize: accumulate finished event pairs
+
+// NVTX range for the solver's host-side phases (iteration chunks, reliable updates, admission,
+// finalization, serving passes): visible in Nsight tools, a no-op without one.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace odwf

@@ -473,6 +473,7 @@ void worker_loop(serve_handle* S) {
             if (g->cg && g->cg->any_running()) act.push_back(g.get());
         lk.unlock();
         bool launched = false;
+        NvtxRange nv_("odwf.serve.pass");
         for (Group* g : act) {
             BatchCG& cg = *g->cg;
             int rc = ODWF_OK;
