@@ -397,7 +397,7 @@ int BatchCG::launch_v2_kernel(int kind, int lo, int n, cudaStream_t s) {
         P.cg_x = Xin.ref();
         P.cg_p = Pl.ref();
     }
-    ODWF_CK(launch_hop2(P, kind, low, lk, n, s));
+    ODWF_CK(launch_hop_prod(P, kind, low, lk, n, s));
     return ODWF_OK;
 }
 
@@ -421,7 +421,7 @@ int BatchCG::launch_v2_hops(int lo, int n, cudaStream_t s) {
         }
         auto pb_ = prof_begin(pcls[k], s);
         P.prof_count = pb_.dev_count;
-        const cudaError_t e_ = launch_hop2(P, k + 1, low, lk, n, s);
+        const cudaError_t e_ = launch_hop_prod(P, k + 1, low, lk, n, s);
         prof_end(pb_, s);
         P.prof_count = nullptr;
         ODWF_CK(e_);

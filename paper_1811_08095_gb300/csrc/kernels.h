@@ -44,6 +44,11 @@ cudaError_t launch_hop_mixed(const HopParams<float>& P, Epi e, Sp low, Lk lk, in
 // (see kernels_mixed2.cu); the non-dagger hops read chi = B psi fields.
 bool hop2_supported(int ns, Sp low, size_t vh);
 cudaError_t launch_hop2(const HopParams<float>& P, int kind, Sp low, Lk lk, int nsys, cudaStream_t st);
+// The hops K1, K2, K3 with two adjacent s per lane (kernels_mixed3.cu): Ns = 8 or 16, FP16 / BF16.
+bool hop3_supported(int ns, Sp low, int kind);
+cudaError_t launch_hop3(const HopParams<float>& P, int kind, Sp low, Lk lk, int nsys, cudaStream_t st);
+// the production hop for this configuration and kind (hop3 where supported, else hop2)
+cudaError_t launch_hop_prod(const HopParams<float>& P, int kind, Sp low, Lk lk, int nsys, cudaStream_t st);
 // p = r (mode 0) or p = r + beta p (mode 1), and chi = B p
 cudaError_t launch_p_update2(Sp low, int ns, const FieldRef& r, const FieldRef& p, const FieldRef& chi,
                              size_t n_sites, int mode, const Coef5<float>& cf, const double* r_sys, SysState* st,

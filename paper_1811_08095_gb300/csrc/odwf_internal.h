@@ -50,10 +50,13 @@ struct Coef5 {
 
 // ---------------------------------------------------------------- storage formats
 // Spinor half field: 24 reals per 5D site in the order [spin][colour][re,im]
-// (spins 0, 1 = P_+ "up", 2, 3 = P_- "down"), stored chunked so that the Ns lanes of
-// a site read consecutive 16-byte words: byte address of chunk k of (h, s) is
-//   ((h * NCH + k) * Ns + s) * 16.
-// Half-precision formats carry one FP32 scale per 5D site: value = stored * scale.
+// (spins 0, 1 = P_+ "up", 2, 3 = P_- "down"), stored chunked so that the lanes of a site read
+// consecutive 16-byte words: byte address of chunk k of (h, s) is
+//   ((h * NCH + k) * Ns + slot(s)) * 16,   slot(s) = s / 2 (s even), Ns / 2 + s / 2 (s odd).
+// The slot order puts the even s of a site first and the odd s second, so that kernels whose
+// lane l holds the adjacent pair s = 2l, 2l + 1 read two runs of consecutive words, as kernels
+// with one s per lane read one.  Half-precision formats carry one FP32 scale per 5D site,
+// value = stored * scale, at norm[h * Ns + s] (not permuted).
 struct SpF64 { using T = double; static constexpr int NCH = 12; static constexpr bool kNorm = false; };
 struct SpF32 { using T = float; static constexpr int NCH = 6; static constexpr bool kNorm = false; };
 struct SpF16 { using T = __half; static constexpr int NCH = 3; static constexpr bool kNorm = true; };
@@ -62,8 +65,10 @@ struct SpBF16 { using T = __nv_bfloat16; static constexpr int NCH = 3; static co
 template <class SP>
 __host__ __device__ constexpr size_t spinor_bytes(size_t sites5) { return sites5 * SP::NCH * 16; }
 
+__host__ __device__ __forceinline__ int chunk_slot(int s, int ns) { return (s & 1) * (ns >> 1) + (s >> 1); }
+
 __device__ __forceinline__ size_t chunk_off(size_t h, int k, int nch, int ns, int s) {
-    return ((h * nch + k) * (size_t)ns + s);
+    return ((h * nch + k) * (size_t)ns + chunk_slot(s, ns));
 }
 
 template <class SP, class R>
