@@ -4,7 +4,7 @@
 // site's Ns/2-lane group holding the 5D sites s = 2l and 2l + 1.  K4, which also streams the FP32
 // CG vectors r and x in and out, stays with one s per lane: at the higher occupancy of that kernel
 // its streams are hidden better (measured on 32^4 x 16, one system: K1 509 -> 422 us, K3 524 ->
-// 425 us, K2 784 -> 763 us here; K4 922 us there against 982 us here).
+// 425 us, K2 784 -> 708 us here; K4 922 us there against 982 us here).
 //
 // Why two s per lane: on GB300 the one-s-per-lane hops are bound by the L1/shared-memory data
 // path, not by HBM.  With two s per lane
@@ -218,8 +218,13 @@ __device__ __forceinline__ void to_pairs(const Acc& a, Half6& up, Half6& dn) {
     }
 }
 
+// Blocks per SM: K2, which also streams p in and keeps two scans' state, runs faster at four
+// (128 registers, a few spilled: 764 -> 708 us on 32^4 x 16); K1 and K3 at three (168 registers).
+template <int KIND>
+constexpr int hop3_min_blocks() { return KIND == K2 ? 4 : 3; }
+
 template <class SP, class LK, int NS, int KIND>
-__global__ void __launch_bounds__(kBS3, 3) hop3_kernel(const HopParams<float> P) {
+__global__ void __launch_bounds__(kBS3, hop3_min_blocks<KIND>()) hop3_kernel(const HopParams<float> P) {
     constexpr int LPS = NS / 2;            // lanes per site
     constexpr int kLS = 18;                // floats per staged link: 9 x (ur, ui)
     constexpr int kSL = 8 * kLS + 4;       // floats per site
