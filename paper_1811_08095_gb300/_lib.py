@@ -14,7 +14,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libodwf.so")
+# ODWF_LIBRARY selects another build of the same C ABI (e.g. the bounds-checked libodwf_check.so)
+LIB_PATH = os.environ.get("ODWF_LIBRARY") or os.path.join(_HERE, "libodwf.so")
 
 ODWF_OK, ODWF_EINVAL, ODWF_ENOMEM, ODWF_ENOCONV, ODWF_EBREAKDOWN, ODWF_ETIMEOUT, ODWF_ECUDA, ODWF_PENDING, \
     ODWF_ENOTFOUND, ODWF_ECANCELED, ODWF_EBUSY = range(11)

@@ -2,7 +2,9 @@
 
 Every translation unit under csrc/ compiles in parallel; the objects link into
 paper_1811_08095_gb300/libodwf.so next to this file.  Rebuilds only when a source
-or header is newer than the library.
+or header is newer than the library.  build(bounds_check=True) makes the debug variant
+libodwf_check.so (ODWF_BOUNDS_CHECK: the kernels check every gathered index and the calls
+report an out-of-range one as ODWF_ECUDA); both variants can be built in one call.
 """
 from __future__ import annotations
 
@@ -16,7 +18,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libodwf.so")
+LIB_CHECK = os.path.join(HERE, "libodwf_check.so")
 BUILD = os.path.join(HERE, "_build")
+BUILD_CHECK = os.path.join(HERE, "_build_check")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -34,31 +38,30 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib=LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
         glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
+def _compile(variants, verbose):
+    """Compile and link every (library, object directory, extra flags) variant, all
+    translation units of all variants in parallel."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
     procs = []
-    objs = []
-    for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        objs.append(obj)
-        cmd = [nvcc] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj]
-        if src.endswith(".cpp"):
-            cmd = [nvcc] + NVCC_FLAGS + ["-x", "cu"] + ARCH + ["-c", src, "-o", obj]
-        if verbose:
-            print(" ".join(cmd), file=sys.stderr)
-        procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    for lib, bdir, extra in variants:
+        os.makedirs(bdir, exist_ok=True)
+        for src in sources():
+            obj = os.path.join(bdir, os.path.basename(src) + ".o")
+            cmd = [nvcc] + ARCH + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
+            if src.endswith(".cpp"):
+                cmd = [nvcc] + NVCC_FLAGS + extra + ["-x", "cu"] + ARCH + ["-c", src, "-o", obj]
+            if verbose:
+                print(" ".join(cmd), file=sys.stderr)
+            procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     failed = []
     for src, p in procs:
         out, _ = p.communicate()
@@ -67,12 +70,24 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         msg = "\n".join("%s:\n%s" % f for f in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    for lib, bdir, _ in variants:
+        objs = [os.path.join(bdir, os.path.basename(src) + ".o") for src in sources()]
+        tmp = lib + ".tmp%d" % os.getpid()
+        subprocess.check_call([nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs)
+        os.replace(tmp, lib)
+
+
+def build(force: bool = False, verbose: bool = False, bounds_check: bool = False) -> str:
+    """Build libodwf.so (and libodwf_check.so when bounds_check) if stale; returns libodwf.so's path."""
+    variants = []
+    if force or _stale(LIB):
+        variants.append((LIB, BUILD, []))
+    if bounds_check and (force or _stale(LIB_CHECK)):
+        variants.append((LIB_CHECK, BUILD_CHECK, ["-DODWF_BOUNDS_CHECK"]))
+    if variants:
+        _compile(variants, verbose)
     return LIB
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, bounds_check="--bounds-check" in sys.argv))

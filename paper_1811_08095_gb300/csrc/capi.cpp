@@ -41,6 +41,14 @@ int on_handle_device(odwf_handle* h, const char* fn, std::initializer_list<const
 }
 }  // namespace
 
+// the call's status, or the debug build's bounds-check error when the call itself succeeded
+#define WITH_BOUNDS(h, call, stream)                                      \
+    do {                                                                  \
+        const int rc0_ = (call);                                          \
+        const int rb_ = (h)->e.bounds_status((cudaStream_t)(stream));     \
+        return rb_ ? rb_ : rc0_;                                          \
+    } while (0)
+
 #define ON_DEVICE(h, fn, ...)                                   \
     do {                                                        \
         const int rc_ = on_handle_device(h, fn, {__VA_ARGS__}); \
@@ -51,7 +59,11 @@ extern "C" {
 
 const char* odwf_last_error(void) { return odwf::last_error(); }
 
-const char* odwf_version(void) { return "odwf-gb300 0.1 (sm_103a)"; }
+#ifdef ODWF_BOUNDS_CHECK
+const char* odwf_version(void) { return "odwf-gb300 0.2 (sm_103a, bounds-checked)"; }
+#else
+const char* odwf_version(void) { return "odwf-gb300 0.2 (sm_103a)"; }
+#endif
 
 int odwf_zolotarev_omega(int Ns, double lmin, double lmax, int variant, double* omega_out, double* dz_out) {
     GUARD_BEGIN
@@ -94,7 +106,7 @@ int odwf_apply(odwf_handle* h, void* out, const void* in, int mode, void* stream
     GUARD_BEGIN
     if (!h) return fail(ODWF_EINVAL, "odwf_apply: null handle");
     ON_DEVICE(h, "odwf_apply", out, in);
-    return h->e.apply(out, in, mode, false, (cudaStream_t)stream);
+    WITH_BOUNDS(h, h->e.apply(out, in, mode, false, (cudaStream_t)stream), stream);
     GUARD_END
 }
 
@@ -102,7 +114,7 @@ int odwf_apply_dagger(odwf_handle* h, void* out, const void* in, int mode, void*
     GUARD_BEGIN
     if (!h) return fail(ODWF_EINVAL, "odwf_apply_dagger: null handle");
     ON_DEVICE(h, "odwf_apply_dagger", out, in);
-    return h->e.apply(out, in, mode, true, (cudaStream_t)stream);
+    WITH_BOUNDS(h, h->e.apply(out, in, mode, true, (cudaStream_t)stream), stream);
     GUARD_END
 }
 
@@ -110,7 +122,7 @@ int odwf_apply_normal(odwf_handle* h, void* out, const void* in, int system, voi
     GUARD_BEGIN
     if (!h) return fail(ODWF_EINVAL, "odwf_apply_normal: null handle");
     ON_DEVICE(h, "odwf_apply_normal", out, in);
-    return h->e.apply_normal(out, in, system, (cudaStream_t)stream);
+    WITH_BOUNDS(h, h->e.apply_normal(out, in, system, (cudaStream_t)stream), stream);
     GUARD_END
 }
 
@@ -118,7 +130,7 @@ int odwf_apply_normal_prec(odwf_handle* h, void* out, const void* in, int prec, 
     GUARD_BEGIN
     if (!h) return fail(ODWF_EINVAL, "odwf_apply_normal_prec: null handle");
     ON_DEVICE(h, "odwf_apply_normal_prec", out, in);
-    return h->e.apply_low_normal(out, in, prec, link_recon, (cudaStream_t)stream);
+    WITH_BOUNDS(h, h->e.apply_low_normal(out, in, prec, link_recon, (cudaStream_t)stream), stream);
     GUARD_END
 }
 
@@ -137,7 +149,7 @@ int odwf_mixed_cg_step(odwf_handle* h, int prec, int link_recon, int link_prec, 
     ON_DEVICE(h, "odwf_mixed_cg_step", p_prev, r, x);
     if (outs)
         for (int i = 0; i < 8; ++i) ON_DEVICE(h, "odwf_mixed_cg_step", outs[i]);
-    return h->e.mixed_cg_step(prec, link_recon, link_prec, mq, p_prev, r, x, outs, sc, (cudaStream_t)stream);
+    WITH_BOUNDS(h, h->e.mixed_cg_step(prec, link_recon, link_prec, mq, p_prev, r, x, outs, sc, (cudaStream_t)stream), stream);
     GUARD_END
 }
 
@@ -157,7 +169,7 @@ int odwf_effective_solve(odwf_handle* h, void* x, const void* b, const odwf_solv
     ON_DEVICE(h, "odwf_effective_solve", x, b);
     const int rc = odwf::check_params(params);
     if (rc) return rc;
-    return h->e.effective_solve(x, b, params, stats, (cudaStream_t)stream);
+    WITH_BOUNDS(h, h->e.effective_solve(x, b, params, stats, (cudaStream_t)stream), stream);
     GUARD_END
 }
 
@@ -168,7 +180,7 @@ int odwf_residual_mass(odwf_handle* h, const int32_t* site, const odwf_solve_par
     ON_DEVICE(h, "odwf_residual_mass");
     const int rc = odwf::check_params(params);
     if (rc) return rc;
-    return h->e.residual_mass(site, params, mres, corr, stats, (cudaStream_t)stream);
+    WITH_BOUNDS(h, h->e.residual_mass(site, params, mres, corr, stats, (cudaStream_t)stream), stream);
     GUARD_END
 }
 
@@ -179,7 +191,7 @@ int odwf_cg_solve(odwf_handle* h, void* x, const void* b, const odwf_solve_param
     ON_DEVICE(h, "odwf_cg_solve", x, b);
     void* xs[1] = {x};
     const void* bs[1] = {b};
-    return h->e.solve(1, xs, bs, nullptr, params, stats, (cudaStream_t)stream);
+    WITH_BOUNDS(h, h->e.solve(1, xs, bs, nullptr, params, stats, (cudaStream_t)stream), stream);
     GUARD_END
 }
 
@@ -191,7 +203,7 @@ int odwf_cg_solve_batched(odwf_handle* h, int nsys, void* const* x, const void* 
         for (int i = 0; i < nsys; ++i) ON_DEVICE(h, "odwf_cg_solve_batched", x[i], b[i]);
     if (params && params->system != ODWF_SYS_SCHUR_NORMAL)
         return fail(ODWF_EINVAL, "odwf_cg_solve_batched: SCHUR_NORMAL only");
-    return h->e.solve(nsys, x, b, mq, params, stats, (cudaStream_t)stream);
+    WITH_BOUNDS(h, h->e.solve(nsys, x, b, mq, params, stats, (cudaStream_t)stream), stream);
     GUARD_END
 }
 

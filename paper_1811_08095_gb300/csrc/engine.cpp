@@ -101,6 +101,23 @@ int Engine::init(const odwf_lattice* l, int Ns, double m0_, double mq_, const do
     if (rc) return rc;
     const double r = mq / (2.0 * m0);
     ODWF_CK(cudaMemcpy(rd, &r, sizeof(double), cudaMemcpyHostToDevice));
+    bounds_flag = (unsigned*)get_ws("bounds_flag", sizeof(unsigned), &rc);
+    if (rc) return rc;
+    ODWF_CK(cudaMemset(bounds_flag, 0, sizeof(unsigned)));
+    return ODWF_OK;
+}
+
+int Engine::bounds_status(cudaStream_t st) {
+#ifdef ODWF_BOUNDS_CHECK
+    unsigned f = 0;
+    ODWF_CK(cudaMemcpyAsync(&f, bounds_flag, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    ODWF_CK(cudaStreamSynchronize(st));
+    if (f)
+        return fail(ODWF_ECUDA, std::string("bounds check: a kernel gathered an index outside its field (flags ") +
+                                    std::to_string(f) + ")");
+#else
+    (void)st;
+#endif
     return ODWF_OK;
 }
 
@@ -240,6 +257,7 @@ HopParams<double> Engine::hop_params<double>(int p_out, const double* r_dev) con
     P.links = links_d18;
     P.r_sys = r_dev;
     P.cf = cf64;
+    P.bounds_flag = bounds_flag;
     return P;
 }
 
@@ -255,6 +273,7 @@ HopParams<float> Engine::hop_params<float>(int p_out, const double* r_dev) const
     P.nbr = nbr;
     P.r_sys = r_dev;
     P.cf = cf32;
+    P.bounds_flag = bounds_flag;
     return P;
 }
 

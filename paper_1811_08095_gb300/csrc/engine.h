@@ -68,6 +68,7 @@ struct Engine {
     void* links_site[4] = {nullptr, nullptr, nullptr, nullptr};  // site-major copies by Lk (second-generation hops)
     bool have_site[4] = {false, false, false, false};
     int* nbr = nullptr;  // neighbour table of the second-generation hops (launch_build_neighbours)
+    unsigned* bounds_flag = nullptr;  // device word for the debug build's index checks
     bool gauge_set = false;
     bool have_f12 = false, have_f18 = false, have_h12 = false;  // low-precision copies of the FP64 links
     const void* links_of(Lk lk) const {
@@ -84,6 +85,8 @@ struct Engine {
     int set_gauge(const void* U, cudaStream_t st);
     int ensure_links(Lk lk, cudaStream_t st);  // FP32 links in format lk, converted on first use
     int ensure_site_links(Lk lk, cudaStream_t st);  // site-major copy of format lk (after ensure_links)
+    // debug builds: ODWF_ECUDA when a kernel recorded an out-of-range index (synchronizes st)
+    int bounds_status(cudaStream_t st);
 
     size_t vh() const { return (size_t)g.Vh; }
     size_t sites5() const { return (size_t)g.Vh * ns; }

@@ -92,6 +92,7 @@ struct HopParams {
     unsigned* counters;         // [sys]
     int sys_base;               // system index offset (blockIdx.y + sys_base)
     unsigned long long* prof_count;  // optional: counts running (system, launch) pairs
+    unsigned* bounds_flag;           // debug builds: where out-of-range indices are recorded
     Coef5<R> cf;
 };
 
@@ -323,7 +324,7 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams<R> P) {
             int cn[4] = {c[0], c[1], c[2], c[3]};
             const int Lm = P.g.L[mu];
             cn[mu] = dir == 0 ? (c[mu] + 1 == Lm ? 0 : c[mu] + 1) : (c[mu] == 0 ? Lm - 1 : c[mu] - 1);
-            const int hn = half_index(P.g, cn);
+            const int hn = checked_index(half_index(P.g, cn), P.g.Vh, P.bounds_flag, kBoundsNeighbour);
             bool flip = false;
             if (mu == 3 && P.g.tbc) flip = dir == 0 ? (c[3] == Lm - 1) : (c[3] == 0);
 

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
         const int raw[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            nb[j] = raw[j] & 0x7fffffff;
+            nb[j] = checked_index(raw[j] & 0x7fffffff, P.g.Vh, P.bounds_flag, kBoundsNeighbour);
             flip |= ((unsigned)raw[j] >> 31) << j;
         }
     }

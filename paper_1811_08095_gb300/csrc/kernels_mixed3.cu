@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kBS3, hop3_min_blocks<KIND>()) hop3_kernel(con
         const int raw[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            nb[j] = raw[j] & 0x7fffffff;
+            nb[j] = checked_index(raw[j] & 0x7fffffff, P.g.Vh, P.bounds_flag, kBoundsNeighbour);
             flip |= ((unsigned)raw[j] >> 31) << j;
         }
     }

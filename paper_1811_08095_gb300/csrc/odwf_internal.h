@@ -269,6 +269,26 @@ struct LinkIO<LinkH12, R> {
     }
 };
 
+// ---------------------------------------------------------------- bounds checks (debug builds)
+// Built with ODWF_BOUNDS_CHECK (libodwf_check.so): an index gathered from a table or computed
+// from coordinates that falls outside [0, n) sets `code` in *flag and is replaced by 0, so that
+// no access leaves its buffer; the host reports the flag as an error after the call.  In the
+// release build this compiles to the index itself.
+__device__ __forceinline__ int checked_index(int i, int n, unsigned* flag, unsigned code) {
+#ifdef ODWF_BOUNDS_CHECK
+    if ((unsigned)i >= (unsigned)n) {
+        if (flag) atomicOr(flag, code);
+        return 0;
+    }
+#else
+    (void)n;
+    (void)flag;
+    (void)code;
+#endif
+    return i;
+}
+enum : unsigned { kBoundsNeighbour = 1u, kBoundsSite = 2u };
+
 // ---------------------------------------------------------------- lane-group shuffles
 template <class R>
 __device__ __forceinline__ R shfl_idx(R v, int src, int width) { return __shfl_sync(0xffffffffu, v, src, width); }

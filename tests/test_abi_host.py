@@ -37,6 +37,19 @@ def test_exports_every_declared_symbol(lib):
         assert hasattr(lib, n), "libodwf.so does not export %s" % n
 
 
+def test_bounds_checked_build_exports_the_same_abi():
+    """The debug variant (ODWF_BOUNDS_CHECK) is built beside the library and exports the same
+    entry points; its version string says it is the checked build."""
+    from paper_1811_08095_gb300 import build as b
+
+    b.build(bounds_check=True)
+    chk = ctypes.CDLL(b.LIB_CHECK)
+    for n in declared_functions():
+        assert hasattr(chk, n), "libodwf_check.so does not export %s" % n
+    chk.odwf_version.restype = ctypes.c_char_p
+    assert b"bounds-checked" in chk.odwf_version()
+
+
 def test_library_is_in_tree(lib):
     assert os.path.dirname(odwf.lib_path()).startswith(ROOT)
 
