@@ -18,7 +18,11 @@ available; these stand in for them):
     paper-scale workloads;
   * right-hand sides with independent unit-Gaussian real and imaginary parts;
   * point sources: a unit spin-colour delta at one seeded site, placed on the
-    domain walls (its negative-chirality spins on s = 1, positive on s = Ns).
+    domain walls (its negative-chirality spins on s = 1, positive on s = Ns);
+  * for the gradient flow: abelian fields diag(e^{i q_1 phi}, e^{i q_2 phi}, e^{i q_3 phi}),
+    q_1 + q_2 + q_3 = 0, carrying n_{mu nu} units of constant flux through every
+    (mu, nu) plane of the torus (optionally times the random links above as noise), and
+    single abelian waves phi_mu(x) = a cos(2 pi n x_nu / L_nu).
 The random stream is numpy's PCG64 `default_rng(seed)`; the large-lattice path uses
 torch's generator on the target device with the same recipe.
 """
@@ -29,7 +33,7 @@ import numpy as np
 __all__ = [
     "gell_mann", "gauge_field", "gauge_field_torch", "gaussian_spinor",
     "gaussian_spinor_even", "point_source", "random_site", "random_even_site", "volume",
-    "even_sites",
+    "even_sites", "flux_field", "abelian_wave_field",
 ]
 
 
@@ -152,3 +156,42 @@ def point_source(ns: int, dims, site, spin: int, color: int) -> np.ndarray:
     s = ns - 1 if spin < 2 else 0
     out[s, t, z, y, x, spin, color] = 1.0
     return out
+
+
+def _abelian_links(phases, charges):
+    """diag(exp(i q_k phi)) for phases (..., ) and integer charges summing to zero."""
+    q = np.asarray(charges, dtype=np.float64)
+    assert q.shape == (3,) and abs(q.sum()) < 1e-12
+    out = np.zeros(phases.shape + (3, 3), dtype=np.complex128)
+    for k in range(3):
+        out[..., k, k] = np.exp(1j * q[k] * phases)
+    return out
+
+
+def flux_field(dims, fluxes, charges=(1, -1, 0)) -> np.ndarray:
+    """Abelian links with n_{mu nu} = fluxes[(mu, nu)] (mu < nu) flux quanta through each
+    (mu, nu) plane: every plaquette of that plane has the phase 2 pi n / (L_mu L_nu) (mod 2 pi).
+
+    phi_mu(x) gets -2 pi n x_nu / (L_mu L_nu); phi_nu(x) gets 2 pi n x_mu / L_mu on the last
+    slice x_nu = L_nu - 1, which closes the flux across the periodic boundary."""
+    lx, ly, lz, lt = dims
+    L = (lx, ly, lz, lt)
+    t, z, y, x = np.meshgrid(np.arange(lt), np.arange(lz), np.arange(ly), np.arange(lx), indexing="ij")
+    X = (x, y, z, t)
+    phi = np.zeros((4, lt, lz, ly, lx))
+    for (mu, nu), n in fluxes.items():
+        assert mu < nu
+        phi[mu] += -2.0 * np.pi * n * X[nu] / (L[mu] * L[nu])
+        phi[nu] += np.where(X[nu] == L[nu] - 1, 2.0 * np.pi * n * X[mu] / L[mu], 0.0)
+    return _abelian_links(phi, charges)
+
+
+def abelian_wave_field(dims, mu: int, nu: int, amp: float, n: int, charges=(1, -1, 0)) -> np.ndarray:
+    """Links equal to 1 except U_mu(x) = diag(exp(i q_k phi(x_nu))), phi = amp cos(2 pi n x_nu / L_nu)."""
+    lx, ly, lz, lt = dims
+    L = (lx, ly, lz, lt)
+    t, z, y, x = np.meshgrid(np.arange(lt), np.arange(lz), np.arange(ly), np.arange(lx), indexing="ij")
+    X = (x, y, z, t)
+    phi = np.zeros((4, lt, lz, ly, lx))
+    phi[mu] = amp * np.cos(2.0 * np.pi * n * X[nu] / L[nu])
+    return _abelian_links(phi, charges)
