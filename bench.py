@@ -165,6 +165,20 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+FLOW_TRAFFIC = os.path.join(ROOT, "profiles", "ncu_traffic_flow.txt")
+
+
+def ncu_traffic_file(path, kernel_class):
+    """DRAM bytes per launch of a kernel class from a committed ncu summary (class bytes ...)."""
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 2 and not line.startswith("#") and parts[0] == kernel_class:
+            return float(parts[1])
+    return None
+
+
 def ncu_traffic(kernel_class):
     """(dram bytes per launch, running systems in that launch) for a kernel class from the
     committed ncu summary, if present."""
@@ -473,6 +487,142 @@ def run_ours(args, world, rank, local):
     h.close()
     if dist:
         dist.destroy_process_group()
+
+
+FLOW_DIMS = (64, 64, 64, 64)
+FLOW_EPS = 0.01
+FLOW_SEGMENT = 10  # Runge-Kutta steps per bench step; one measurement closes each segment
+FLOW_GAUGE_EPS = 0.2
+FLOW_WORKLOAD = "wilson_flow_64x64x64x64_eps0.01"
+
+
+def run_flow(args, world, rank, local):
+    """Gradient flow on the paper's 64^4 lattice (Sec. 2-3: step 0.01, E(t) for t0, clover Q and
+    the admissibility minimum).  A bench step is FLOW_SEGMENT Runge-Kutta steps followed by one
+    measurement; the metric is flow steps per second.  Every rank flows its own field (replicas)."""
+    import numpy as np
+    import torch
+
+    import odwf_synth as syn
+    import paper_1811_08095_gb300 as odwf
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = odwf.load()
+    stream = torch.cuda.current_stream()
+    dims = tuple(args.flow_dims)
+    V = math.prod(dims)
+    U = syn.gauge_field_torch(dims, FLOW_GAUGE_EPS, 3, device=dev)
+    f = odwf.Flow(dims)
+    f.set_gauge(U, stream=stream)
+    t = 0.0
+    obs = [f.measure(t, stream=stream)]
+
+    def segment(t):
+        f.run(FLOW_EPS, FLOW_SEGMENT, measure_every=0, t_start=t, stream=stream)
+        t += FLOW_SEGMENT * FLOW_EPS
+        return t, f.measure(t, stream=stream)
+
+    for _ in range(args.warmup):
+        t, o = segment(t)
+        obs.append(o)
+    torch.cuda.synchronize()
+    launches0 = lib.odwf_launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    seg_ms = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t, o = segment(t)
+        e1.record(stream)
+        e1.synchronize()
+        seg_ms.append(e0.elapsed_time(e1))
+        obs.append(o)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = lib.odwf_launch_count() - launches0
+
+    # per-launch events over one more segment (the roofline's kernel durations)
+    lib.odwf_profile_enable(1)
+    t, o = segment(t)
+    obs.append(o)
+    torch.cuda.synchronize()
+    prof = read_profile(lib)
+    lib.odwf_profile_enable(0)
+    peak, peak_kind = measured_peaks()
+    kernels = {}
+    for e in prof:
+        tot = e["launches"] * e["bytes_per_launch"]
+        kernels[e["name"]] = {"launches": e["launches"], "avg_us": round(1e3 * e["total_ms"] / max(1, e["launches"]), 1),
+                              "algorithmic_bytes_per_launch": e["bytes_per_launch"],
+                              "gbs": round(tot / (e["total_ms"] / 1e3) / 1e9, 1) if e["total_ms"] > 0 else 0.0}
+    dom = max(prof, key=lambda e: e["total_ms"])
+    avg_s = dom["total_ms"] / dom["launches"] / 1e3
+    achieved = dom["bytes_per_launch"] / avg_s / 1e9
+    tr = None
+    cap = ncu_traffic_file(FLOW_TRAFFIC, dom["name"])
+    if cap:
+        tr = round(cap)
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": tr, "kernel": dom["name"],
+            "algorithmic_bytes_per_launch": dom["bytes_per_launch"],
+            "timing": "per-launch CUDA events on the launching stream over one extra segment",
+            "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)"}
+
+    # end to end: the field from pinned host memory, one segment, the observables back
+    Uh = U.cpu().pin_memory()
+    del U
+    torch.cuda.empty_cache()
+    f.set_gauge(Uh.numpy(), stream=stream)
+    torch.cuda.synchronize()
+    t_e = time.perf_counter()
+    for _ in range(args.steps):
+        f.set_gauge(Uh.numpy(), stream=stream)
+        segment(0.0)
+    e2e_s = time.perf_counter() - t_e
+    e2e = {"value": round(args.steps * FLOW_SEGMENT * world / e2e_s, 3), "unit": "flow steps/s",
+           "h2d_bytes_per_step": Uh.numel() * Uh.element_size(), "d2h_bytes_per_step": 48}
+    f.close()
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        from oracle import flow as ofl
+
+        sample = (8, 8, 8, 8)
+        Us = syn.gauge_field(sample, FLOW_GAUGE_EPS, 3)
+        t_c = time.perf_counter()
+        ofl.rk3_step(Us, FLOW_EPS)
+        sec = time.perf_counter() - t_c
+        per_site = sec / math.prod(sample)
+        cpu = {"value": round(1.0 / (per_site * V), 8), "unit": "flow steps/s", "cores": 1, "kind": "oracle",
+               "sample": "one oracle Runge-Kutta step on an 8^4 field of the same recipe (%.2f s, numpy in one "
+                         "thread), scaled by the site count to %s" % (sec, "x".join(map(str, dims)))}
+
+    seg = sum(seg_ms) / len(seg_ms)
+    value = world * FLOW_SEGMENT / (seg / 1e3)
+    if rank == 0:
+        line = {
+            "metric": "gradient-flow Runge-Kutta steps/s on %s (eps 0.01), E / Q_clover / admissibility measured "
+                      "every 10 steps" % "x".join(map(str, dims)),
+            "value": round(value, 3), "unit": "flow steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(seg, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (links as float-float pairs)", "data": "synthetic",
+            "config": {"workload": FLOW_WORKLOAD if dims == FLOW_DIMS else "wilson_flow_%s_eps0.01" % "x".join(
+                           map(str, dims)), "lattice": "x".join(map(str, dims)), "eps": FLOW_EPS,
+                       "step": "%d Runge-Kutta steps + one measurement" % FLOW_SEGMENT,
+                       "gauge": "U = exp(0.2 i H), H Gaussian traceless Hermitian (seed 3)",
+                       "site_steps_per_s": round(value * V, 1),
+                       "l2": "not flushed: the flow's working set (%.1f GB) exceeds L2" % (1472 * V / 1e9),
+                       "parallelism": "replicas only" if world > 1 else "single GPU",
+                       "observables": [{k: (round(v, 8) if isinstance(v, float) else v) for k, v in o.items()}
+                                       for o in (obs[0], obs[-1])]},
+            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
 
 
 SERVE_LATTICES = [(8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 48), (32, 32, 32, 32)]
@@ -840,12 +990,13 @@ def main():
     ap.add_argument("--delta", type=float, default=0.01, help="reliable-update threshold")
     ap.add_argument("--link-recon", type=int, default=12, choices=[12, 18])
     ap.add_argument("--check-every", type=int, default=8, help="iterations between host polls of the solver state")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "serve", "profile", "mres", "dslash"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "serve", "profile", "mres", "dslash", "flow"],
                     help="c2: the default line; c3: 36-system batch on 24^3x48; c5: one 64^4 solve; serve; "
-                         "profile: a fixed short solver run for ncu")
+                         "profile: a fixed short solver run for ncu; flow: gradient flow on 64^4")
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS), help="profile: lattice")
     ap.add_argument("--ns", type=int, default=NS, help="profile: Ns")
     ap.add_argument("--nsys", type=int, default=3, help="profile: systems")
+    ap.add_argument("--flow-dims", type=int, nargs=4, default=list(FLOW_DIMS), help="flow: lattice")
     ap.add_argument("--iters", type=int, default=4, help="profile: CG iterations")
     ap.add_argument("--rate", type=float, default=50.0, help="serve: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
@@ -870,6 +1021,8 @@ def main():
         run_profile_case(args, world, rank, local)
     elif args.workload == "mres":
         run_residual_mass(args, world, rank, local)
+    elif args.workload == "flow":
+        run_flow(args, world, rank, local)
     elif args.workload == "dslash":
         import torch
 

@@ -17,7 +17,7 @@ from ._lib import (ODWF_BF16, ODWF_F16, ODWF_F32, ODWF_F64, ODWF_MODE_FULL, ODWF
                    ODWF_OMEGA_PLAIN, ODWF_OMEGA_SHIFTED_R5, ODWF_SYS_FULL_DIRAC, ODWF_SYS_FULL_NORMAL,
                    ODWF_SYS_SCHUR_NORMAL, OdwfError, check, ptr, stream_ptr)
 
-__all__ = ["Handle", "Server", "odwf_zolotarev_omega", "OdwfError", "ODWF_F64", "ODWF_F32", "ODWF_F16",
+__all__ = ["Handle", "Server", "Flow", "odwf_flow_t0", "odwf_zolotarev_omega", "OdwfError", "ODWF_F64", "ODWF_F32", "ODWF_F16",
            "ODWF_BF16", "ODWF_MODE_FULL", "ODWF_MODE_SCHUR_EVEN", "ODWF_SYS_SCHUR_NORMAL",
            "ODWF_SYS_FULL_NORMAL", "ODWF_SYS_FULL_DIRAC", "ODWF_OMEGA_SHIFTED_R5", "ODWF_OMEGA_PLAIN",
            "load", "lib_path"]
@@ -44,6 +44,84 @@ def odwf_zolotarev_omega(ns: int, lmin: float, lmax: float, variant: int = ODWF_
     check(_lib.load().odwf_zolotarev_omega(int(ns), float(lmin), float(lmax), int(variant), ptr(out),
                                            ctypes.byref(dz)))
     return out, dz.value
+
+
+def _obs_dict(o):
+    return {k: getattr(o, k) for k, _ in _lib.odwf_flow_obs._fields_}
+
+
+def odwf_flow_t0(obs, target: float = 0.3):
+    """Flow time where t^2 <E_clover> first reaches `target` (host interpolation between the two
+    bracketing records of `obs`, a list of measurement dicts), or None when it is not reached."""
+    arr = (_lib.odwf_flow_obs * max(1, len(obs)))()
+    for i, o in enumerate(obs):
+        for k, _ in _lib.odwf_flow_obs._fields_:
+            setattr(arr[i], k, float(o[k]))
+    t0 = ctypes.c_double(0.0)
+    rc = _lib.load().odwf_flow_t0(arr, len(obs), float(target), ctypes.byref(t0))
+    if rc == _lib.ODWF_ENOTFOUND:
+        return None
+    check(rc)
+    return t0.value
+
+
+class Flow:
+    """Gradient flow of a gauge field and its observables (odwf_flow_create ... odwf_flow_destroy)."""
+
+    def __init__(self, dims):
+        self._lib = _lib.load()
+        self.dims = tuple(int(d) for d in dims)
+        d = (ctypes.c_int32 * 4)(*self.dims)
+        h = ctypes.c_void_p()
+        check(self._lib.odwf_flow_create(d, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def volume(self):
+        return math.prod(self.dims)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.odwf_flow_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_gauge(self, U, stream=None):
+        check(self._lib.odwf_flow_set_gauge(self._h, ptr(U), stream_ptr(stream)))
+
+    def get_gauge(self, U, stream=None):
+        check(self._lib.odwf_flow_get_gauge(self._h, ptr(U), stream_ptr(stream)))
+        return U
+
+    def measure(self, t=0.0, e_site=None, q_site=None, stream=None):
+        o = _lib.odwf_flow_obs()
+        check(self._lib.odwf_flow_measure(self._h, float(t), ctypes.byref(o), ptr(e_site), ptr(q_site),
+                                          stream_ptr(stream)))
+        return _obs_dict(o)
+
+    def run(self, eps, nsteps, measure_every=0, t_start=0.0, stream=None):
+        """Integrate nsteps flow steps; returns the list of measurements (empty when
+        measure_every is 0)."""
+        need = 0
+        if measure_every > 0:
+            need = (nsteps - 1) // measure_every + 1 if nsteps > 0 else 0
+            need += 1 if nsteps % measure_every == 0 else 0
+        arr = (_lib.odwf_flow_obs * max(1, need))()
+        n = ctypes.c_int(0)
+        check(self._lib.odwf_flow_run(self._h, float(eps), int(nsteps), int(measure_every), float(t_start), arr,
+                                      need, ctypes.byref(n), stream_ptr(stream)))
+        return [_obs_dict(arr[i]) for i in range(n.value)]
 
 
 def _lattice(dims, t_antiperiodic):

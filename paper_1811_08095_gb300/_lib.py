@@ -67,6 +67,11 @@ class odwf_cg_step_scalars(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class odwf_flow_obs(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("e_plaq", ctypes.c_double), ("e_clover", ctypes.c_double),
+                ("q_clover", ctypes.c_double), ("plaq_min", ctypes.c_double), ("plaq_mean", ctypes.c_double)]
+
+
 class OdwfError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("%s (%d): %s" % (STATUS_NAMES.get(code, "?"), code, msg))
@@ -109,6 +114,13 @@ _SIGS = {
     "serve_destroy": ([P], I),
     "serve_set_policy": ([P, D, I, I], I),
     "serve_cancel": ([P, ctypes.c_uint64], I),
+    "odwf_flow_create": ([ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(P)], I),
+    "odwf_flow_destroy": ([P], I),
+    "odwf_flow_set_gauge": ([P, P, P], I),
+    "odwf_flow_get_gauge": ([P, P, P], I),
+    "odwf_flow_measure": ([P, D, ctypes.POINTER(odwf_flow_obs), P, P, P], I),
+    "odwf_flow_run": ([P, D, I, I, D, ctypes.POINTER(odwf_flow_obs), I, ctypes.POINTER(I), P], I),
+    "odwf_flow_t0": ([ctypes.POINTER(odwf_flow_obs), I, D, ctypes.POINTER(D)], I),
 }
 
 

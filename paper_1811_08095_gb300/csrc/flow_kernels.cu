@@ -1,0 +1,633 @@
+// Gradient flow of the gauge field and the flow observables (Sec. 2 scale condition t^2 <E> = 0.3;
+// Sec. 3 admissibility bound and clover topological charge).
+//
+// Definitions (lattice spacing 1, mu = 0..3 <-> x, y, z, t):
+//   P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+          plaquette
+//   ta(X)        = (X - X^+)/2 - tr(X - X^+)/6                          traceless anti-Hermitian part
+//   Z_mu(x)      = -ta(U_mu(x) S_mu(x))                                 flow force (S_mu: staple sum)
+//   dV/dt        = Z(V) V, third-order Runge-Kutta scheme of Luscher (JHEP 2010), three stages
+//                  W <- exp(X_i) W with X_0 = eps Z_0 / 4, X_1 = 8/9 eps Z_1 - 17/36 eps Z_0,
+//                  X_2 = 3/4 eps Z_2 - X_1
+//   F_{mu nu}(x) = clover field strength from the four plaquette loops around x (Sec. 3)
+//
+// GB300 layout and arithmetic:
+//   * links as float-float pairs (hi + lo, two FP32 arrays [mu][9][V] of complex float2): the
+//     stencils read only hi (FP32); the stage update adds its FP32 increment into (hi, lo) with an
+//     error-free two-sum, so the accumulated links keep ~48 bits over thousands of stages without
+//     any FP64 arithmetic (the FP64 pipe of this part runs at a small fraction of FP32);
+//   * per stage two kernels.  plaq_kernel writes A_{mu nu}(x) = ta(P_{mu nu}(x)) for the six planes
+//     (8 reals each, FP32).  update_kernel assembles the force from A at x and at x - nu:
+//        ta(U_mu(x) S_mu(x)) = sum_nu [A_{mu nu}(x) - U_nu(x-nu)^+ A_{mu nu}(x-nu) U_nu(x-nu)]
+//     (the lower staple loop is the plaquette at x - nu transported to x and reversed), forms the
+//     stage exponent, exponentiates it in closed form (Cayley-Hamilton) and updates its own links
+//     into the other buffer of a ping-pong pair (neighbours still read the old links);
+//   * the clover field is assembled from the same A: each leaf is a plaquette transported to x,
+//     so F_{mu nu}(x) = -i/4 [A(x) + T_{-mu} A(x-mu) + T_{-nu} A(x-nu) + T_{-mu-nu} A(x-mu-nu)];
+//   * sites are visited in slabs of bt time slices, (x, y) planes fastest, then t inside a slab,
+//     then z, so that the t-neighbours a stencil reads are a few planes away (L2 hits) even when
+//     one time slice of links is larger than L2;
+//   * lattice sums: per block in FP64, then one block sums the partials in a fixed order
+//     (deterministic), writing one observable record on the device.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "flow.h"
+
+namespace odwf {
+namespace flow {
+namespace {
+
+constexpr int kBS = 128;
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+// conj(a) * b
+__device__ __forceinline__ float2 ccmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+
+struct M3 {
+    float2 m[9];  // row-major
+};
+
+// traceless anti-Hermitian 3x3: diag i(d0, d1, -d0-d1), upper z01, z02, z12 (lower = -conj)
+struct AH {
+    float d0, d1;
+    float2 z01, z02, z12;
+};
+
+__device__ __forceinline__ M3 mul(const M3& a, const M3& b) {
+    M3 c;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float2 s = cmul(a.m[3 * i], b.m[j]);
+            s = cadd(s, cmul(a.m[3 * i + 1], b.m[3 + j]));
+            s = cadd(s, cmul(a.m[3 * i + 2], b.m[6 + j]));
+            c.m[3 * i + j] = s;
+        }
+    return c;
+}
+
+// ta(a b^+): entries (a b^+)_ij = sum_k a_ik conj(b_jk); also Re tr(a b^+)
+__device__ __forceinline__ AH ta_mul_dag(const M3& a, const M3& b, float* retr) {
+    float2 p[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float2 s = cmulc(a.m[3 * i], b.m[3 * j]);
+            s = cadd(s, cmulc(a.m[3 * i + 1], b.m[3 * j + 1]));
+            s = cadd(s, cmulc(a.m[3 * i + 2], b.m[3 * j + 2]));
+            p[i][j] = s;
+        }
+    *retr = p[0][0].x + p[1][1].x + p[2][2].x;
+    const float im3 = (p[0][0].y + p[1][1].y + p[2][2].y) * (1.0f / 3.0f);
+    AH r;
+    r.d0 = p[0][0].y - im3;
+    r.d1 = p[1][1].y - im3;
+    r.z01 = make_float2(0.5f * (p[0][1].x - p[1][0].x), 0.5f * (p[0][1].y + p[1][0].y));
+    r.z02 = make_float2(0.5f * (p[0][2].x - p[2][0].x), 0.5f * (p[0][2].y + p[2][0].y));
+    r.z12 = make_float2(0.5f * (p[1][2].x - p[2][1].x), 0.5f * (p[1][2].y + p[2][1].y));
+    return r;
+}
+
+__device__ __forceinline__ M3 ah_full(const AH& a) {
+    M3 m;
+    m.m[0] = make_float2(0.f, a.d0);
+    m.m[1] = a.z01;
+    m.m[2] = a.z02;
+    m.m[3] = make_float2(-a.z01.x, a.z01.y);
+    m.m[4] = make_float2(0.f, a.d1);
+    m.m[5] = a.z12;
+    m.m[6] = make_float2(-a.z02.x, a.z02.y);
+    m.m[7] = make_float2(-a.z12.x, a.z12.y);
+    m.m[8] = make_float2(0.f, -a.d0 - a.d1);
+    return m;
+}
+
+// ta(u^+ a u) for anti-Hermitian traceless a (the result is already anti-Hermitian; the
+// projection only removes the rounding in its trace)
+__device__ __forceinline__ AH conj_by(const M3& u, const AH& a) {
+    const M3 A = ah_full(a);
+    const M3 T = mul(A, u);  // a u
+    // C_ij = sum_k conj(u_ki) T_kj
+    float2 c[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            float2 s = ccmul(u.m[i], T.m[j]);
+            s = cadd(s, ccmul(u.m[3 + i], T.m[3 + j]));
+            s = cadd(s, ccmul(u.m[6 + i], T.m[6 + j]));
+            c[i][j] = s;
+        }
+    const float im3 = (c[0][0].y + c[1][1].y + c[2][2].y) * (1.0f / 3.0f);
+    AH r;
+    r.d0 = c[0][0].y - im3;
+    r.d1 = c[1][1].y - im3;
+    r.z01 = c[0][1];
+    r.z02 = c[0][2];
+    r.z12 = c[1][2];
+    return r;
+}
+
+__device__ __forceinline__ void ah_axpy(AH& y, float s, const AH& x) {
+    y.d0 = fmaf(s, x.d0, y.d0);
+    y.d1 = fmaf(s, x.d1, y.d1);
+    y.z01.x = fmaf(s, x.z01.x, y.z01.x);
+    y.z01.y = fmaf(s, x.z01.y, y.z01.y);
+    y.z02.x = fmaf(s, x.z02.x, y.z02.x);
+    y.z02.y = fmaf(s, x.z02.y, y.z02.y);
+    y.z12.x = fmaf(s, x.z12.x, y.z12.x);
+    y.z12.y = fmaf(s, x.z12.y, y.z12.y);
+}
+
+__device__ __forceinline__ AH ah_zero() {
+    AH r;
+    r.d0 = r.d1 = 0.f;
+    r.z01 = r.z02 = r.z12 = make_float2(0.f, 0.f);
+    return r;
+}
+
+// -tr(a b) for traceless anti-Hermitian a, b: sum_i a_i b_i + 2 sum_{i<j} Re(a_ij conj(b_ij))
+__device__ __forceinline__ float ah_dot(const AH& a, const AH& b) {
+    const float a2 = -a.d0 - a.d1, b2 = -b.d0 - b.d1;
+    float s = a.d0 * b.d0 + a.d1 * b.d1 + a2 * b2;
+    s += 2.f * (a.z01.x * b.z01.x + a.z01.y * b.z01.y + a.z02.x * b.z02.x + a.z02.y * b.z02.y +
+                a.z12.x * b.z12.x + a.z12.y * b.z12.y);
+    return s;
+}
+
+__device__ __forceinline__ int plane_of(int mu, int nu) {  // mu < nu
+    return mu == 0 ? nu - 1 : (mu == 1 ? nu + 1 : 5);
+}
+
+// ---------------------------------------------------------------------------------------------
+// site traversal and neighbours
+
+struct Site {
+    size_t s;  // lexicographic index
+    int c[4];
+};
+
+__device__ __forceinline__ bool site_of(const FlowGeom& g, size_t i, Site& st) {
+    if (i >= g.V) return false;
+    const size_t P = (size_t)g.L[0] * g.L[1];
+    const size_t k = i / P;
+    const size_t j = i - k * P;
+    const size_t lzbt = (size_t)g.L[2] * g.bt;
+    const size_t slab = k / lzbt;
+    const int r = (int)(k - slab * lzbt);
+    const int z = r / g.bt;
+    const int t = (int)(slab * g.bt) + (r - z * g.bt);
+    st.c[0] = (int)(j % g.L[0]);
+    st.c[1] = (int)(j / g.L[0]);
+    st.c[2] = z;
+    st.c[3] = t;
+    st.s = j + P * ((size_t)z + (size_t)g.L[2] * t);
+    return true;
+}
+
+__device__ __forceinline__ size_t step(const FlowGeom& g, const Site& st, int mu, int dir) {
+    const int x = st.c[mu];
+    if (dir > 0) return x + 1 == g.L[mu] ? st.s - (size_t)(g.L[mu] - 1) * g.stride[mu] : st.s + g.stride[mu];
+    return x == 0 ? st.s + (size_t)(g.L[mu] - 1) * g.stride[mu] : st.s - g.stride[mu];
+}
+
+// step from an arbitrary lexicographic index whose coordinate along mu is x
+__device__ __forceinline__ size_t step_from(const FlowGeom& g, size_t s, int x, int mu, int dir) {
+    if (dir > 0) return x + 1 == g.L[mu] ? s - (size_t)(g.L[mu] - 1) * g.stride[mu] : s + g.stride[mu];
+    return x == 0 ? s + (size_t)(g.L[mu] - 1) * g.stride[mu] : s - g.stride[mu];
+}
+
+__device__ __forceinline__ M3 load_link(const float2* __restrict__ hi, size_t V, int mu, size_t s) {
+    M3 u;
+    const float2* p = hi + (size_t)mu * 9 * V + s;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u.m[k] = __ldg(p + (size_t)k * V);
+    return u;
+}
+
+__device__ __forceinline__ AH load_ah(const float4* __restrict__ A, size_t V, int p, size_t s) {
+    const float4 a = __ldg(A + (size_t)(2 * p) * V + s);
+    const float4 b = __ldg(A + (size_t)(2 * p + 1) * V + s);
+    AH r;
+    r.d0 = a.x;
+    r.d1 = a.y;
+    r.z01 = make_float2(a.z, a.w);
+    r.z02 = make_float2(b.x, b.y);
+    r.z12 = make_float2(b.z, b.w);
+    return r;
+}
+
+// the carried stage combination K is read and then rewritten by the same thread: plain loads
+__device__ __forceinline__ AH load_ah_rw(const float4* A, size_t V, int p, size_t s) {
+    const float4 a = A[(size_t)(2 * p) * V + s];
+    const float4 b = A[(size_t)(2 * p + 1) * V + s];
+    AH r;
+    r.d0 = a.x;
+    r.d1 = a.y;
+    r.z01 = make_float2(a.z, a.w);
+    r.z02 = make_float2(b.x, b.y);
+    r.z12 = make_float2(b.z, b.w);
+    return r;
+}
+
+__device__ __forceinline__ void store_ah(float4* A, size_t V, int p, size_t s, const AH& r) {
+    A[(size_t)(2 * p) * V + s] = make_float4(r.d0, r.d1, r.z01.x, r.z01.y);
+    A[(size_t)(2 * p + 1) * V + s] = make_float4(r.z02.x, r.z02.y, r.z12.x, r.z12.y);
+}
+
+// ---------------------------------------------------------------------------------------------
+// block reductions (fixed order)
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <int NT>
+__device__ __forceinline__ void block_sum2(double a, double b, double* out_a, double* out_b) {
+    __shared__ double sa[NT / 32], sb[NT / 32];
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sa[w] = a;
+        sb[w] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0, tb = 0;
+        for (int i = 0; i < NT / 32; ++i) {
+            ta += sa[i];
+            tb += sb[i];
+        }
+        *out_a = ta;
+        *out_b = tb;
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void block_sum_min(double a, float m, double* out_a, float* out_m) {
+    __shared__ double sa[NT / 32];
+    __shared__ float sm[NT / 32];
+    a = warp_sum(a);
+    m = warp_min(m);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sa[w] = a;
+        sm[w] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0;
+        float tm = sm[0];
+        for (int i = 0; i < NT / 32; ++i) {
+            ta += sa[i];
+            tm = fminf(tm, sm[i]);
+        }
+        *out_a = ta;
+        *out_m = tm;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// kernels
+
+// A_{mu nu}(x) = ta(P_{mu nu}(x)) for the six planes; with MEASURE, per-block sum and minimum of
+// Re tr P over the block's plaquettes.
+template <bool MEASURE>
+__global__ void __launch_bounds__(kBS) plaq_kernel(FlowGeom g, const float2* __restrict__ hi, float4* __restrict__ A,
+                                                   double* __restrict__ part_retr, float* __restrict__ part_min) {
+    Site st;
+    const bool ok = site_of(g, (size_t)blockIdx.x * kBS + threadIdx.x, st);
+    double rsum = 0.0;
+    float rmin = 3.0f;
+    if (ok) {
+#pragma unroll
+        for (int mu = 0; mu < 3; ++mu) {
+            const M3 um = load_link(hi, g.V, mu, st.s);
+            const size_t xm = step(g, st, mu, +1);
+#pragma unroll
+            for (int nu = mu + 1; nu < 4; ++nu) {
+                const size_t xn = step(g, st, nu, +1);
+                const M3 t1 = mul(um, load_link(hi, g.V, nu, xm));                   // U_mu(x) U_nu(x+mu)
+                const M3 t2 = mul(load_link(hi, g.V, nu, st.s), load_link(hi, g.V, mu, xn));  // U_nu(x) U_mu(x+nu)
+                float retr;
+                const AH a = ta_mul_dag(t1, t2, &retr);
+                store_ah(A, g.V, plane_of(mu, nu), st.s, a);
+                if (MEASURE) {
+                    rsum += retr;
+                    rmin = fminf(rmin, retr);
+                }
+            }
+        }
+    }
+    if (MEASURE) block_sum_min<kBS>(rsum, rmin, part_retr + blockIdx.x, part_min + blockIdx.x);
+}
+
+// exp(X) - 1 for traceless anti-Hermitian X by Cayley-Hamilton: X^3 = s X + d 1 with
+// s = tr(X^2)/2 and d = tr(X^3)/3, so X^n = a_n 1 + b_n X + c_n X^2 with
+// (a, b, c)_{n+1} = (c_n d, a_n + c_n s, b_n); the exponential series is summed on the scalars
+// until the terms fall below 1e-10 of the leading ones.
+__device__ __forceinline__ M3 expm1_ah(const AH& x) {
+    const M3 X = ah_full(x);
+    const M3 X2 = mul(X, X);
+    const float s = 0.5f * (X2.m[0].x + X2.m[4].x + X2.m[8].x);
+    // d = tr(X X2) / 3 (purely imaginary for anti-Hermitian X)
+    float dim = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float2 p = cmul(X.m[3 * i + k], X2.m[3 * k + i]);
+            dim += p.y;
+        }
+    dim *= (1.0f / 3.0f);
+    const float nrm = sqrtf(fmaxf(-2.0f * s, 0.f));  // Frobenius norm of X
+    // the n = 1 and n = 2 terms (X and X^2/2) are in f1, f2; (a, b, c) holds the state of n = 2
+    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f), c = make_float2(1.f, 0.f);
+    float2 f0 = make_float2(0.f, 0.f), f1 = make_float2(1.f, 0.f), f2 = make_float2(0.5f, 0.f);
+    float inv_fact = 0.5f, bound = 0.5f * nrm * nrm;
+#pragma unroll 1
+    for (int n = 3; n < 64; ++n) {
+        // (a, b, c) <- (c d, a + c s, b), d = i dim
+        const float2 na = make_float2(-c.y * dim, c.x * dim);
+        const float2 nb = make_float2(fmaf(c.x, s, a.x), fmaf(c.y, s, a.y));
+        a = na;
+        c = b;
+        b = nb;
+        inv_fact /= (float)n;
+        f0.x = fmaf(a.x, inv_fact, f0.x);
+        f0.y = fmaf(a.y, inv_fact, f0.y);
+        f1.x = fmaf(b.x, inv_fact, f1.x);
+        f1.y = fmaf(b.y, inv_fact, f1.y);
+        f2.x = fmaf(c.x, inv_fact, f2.x);
+        f2.y = fmaf(c.y, inv_fact, f2.y);
+        bound *= nrm / (float)n;
+        if (bound < 1e-10f * fmaxf(nrm, 1e-30f) || bound == 0.f) break;
+    }
+    M3 e;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) e.m[k] = cadd(cmul(f1, X.m[k]), cmul(f2, X2.m[k]));
+    e.m[0] = cadd(e.m[0], f0);
+    e.m[4] = cadd(e.m[4], f0);
+    e.m[8] = cadd(e.m[8], f0);
+    return e;
+}
+
+// error-free hi + d, with the rounding error carried into lo
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float d) {
+    const float s = hi + d;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (d - bb);
+    const float l = lo + err;
+    const float h2 = s + l;
+    lo = l - (h2 - s);
+    hi = h2;
+}
+
+// One Runge-Kutta stage: force from A, exponent X (and the carried combination K), and the
+// update W <- exp(X) W into the other link buffer.
+template <int STAGE>
+__global__ void __launch_bounds__(kBS) update_kernel(FlowGeom g, const float2* __restrict__ hi, const float2* __restrict__ lo,
+                                                     float2* __restrict__ hi_out, float2* __restrict__ lo_out,
+                                                     const float4* __restrict__ A, float4* __restrict__ K, float eps) {
+    Site st;
+    if (!site_of(g, (size_t)blockIdx.x * kBS + threadIdx.x, st)) return;
+    // ta(U_mu S_mu) = sum_nu [A_{mu nu}(x) - U_nu(x-nu)^+ A_{mu nu}(x-nu) U_nu(x-nu)]; Z = -that
+    AH z[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) z[mu] = ah_zero();
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu)
+#pragma unroll
+        for (int nu = mu + 1; nu < 4; ++nu) {
+            const AH a = load_ah(A, g.V, plane_of(mu, nu), st.s);
+            ah_axpy(z[mu], -1.f, a);  // -A_{mu nu}
+            ah_axpy(z[nu], 1.f, a);   // -A_{nu mu} = +A_{mu nu}
+        }
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu) {
+        const size_t xb = step(g, st, nu, -1);
+        const M3 u = load_link(hi, g.V, nu, xb);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            if (mu == nu) continue;
+            const int p = mu < nu ? plane_of(mu, nu) : plane_of(nu, mu);
+            const AH c = conj_by(u, load_ah(A, g.V, p, xb));
+            ah_axpy(z[mu], mu < nu ? 1.f : -1.f, c);  // + U^+ A_{mu nu} U, A_{mu nu} = -A_{nu mu}
+        }
+    }
+    constexpr float cz = STAGE == 0 ? 0.25f : (STAGE == 1 ? 8.0f / 9.0f : 0.75f);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        AH x = ah_zero();
+        ah_axpy(x, cz * eps, z[mu]);
+        if (STAGE > 0) {
+            const AH k = load_ah_rw(K, g.V, mu, st.s);
+            ah_axpy(x, STAGE == 1 ? -17.0f / 36.0f : -1.0f, k);
+        }
+        if (STAGE == 0) {
+            AH k = ah_zero();
+            ah_axpy(k, eps, z[mu]);
+            store_ah(K, g.V, mu, st.s, k);
+        } else if (STAGE == 1) {
+            store_ah(K, g.V, mu, st.s, x);
+        }
+        const M3 e1 = expm1_ah(x);
+        const size_t base = (size_t)mu * 9 * g.V + st.s;
+        M3 w;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) w.m[k] = __ldg(hi + base + (size_t)k * g.V);
+        const M3 d = mul(e1, w);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            float2 h = w.m[k];
+            float2 l = __ldg(lo + base + (size_t)k * g.V);
+            ff_add(h.x, l.x, d.m[k].x);
+            ff_add(h.y, l.y, d.m[k].y);
+            hi_out[base + (size_t)k * g.V] = h;
+            lo_out[base + (size_t)k * g.V] = l;
+        }
+    }
+}
+
+// Clover field strength from A and the per-site energy density and charge density; per-block
+// sums (and optional per-site outputs).
+__global__ void __launch_bounds__(kBS, 2) clover_kernel(FlowGeom g, const float2* __restrict__ hi,
+                                                        const float4* __restrict__ A, double* __restrict__ part_e,
+                                                        double* __restrict__ part_q, float* __restrict__ e_site,
+                                                        float* __restrict__ q_site) {
+    Site st;
+    const bool ok = site_of(g, (size_t)blockIdx.x * kBS + threadIdx.x, st);
+    double e = 0.0, q = 0.0;
+    if (ok) {
+        AH f[6];
+#pragma unroll
+        for (int mu = 0; mu < 3; ++mu) {
+            const size_t xm = step(g, st, mu, -1);
+            const M3 u1 = load_link(hi, g.V, mu, xm);  // U_mu(x-mu)
+#pragma unroll
+            for (int nu = mu + 1; nu < 4; ++nu) {
+                const int p = plane_of(mu, nu);
+                const size_t xn = step(g, st, nu, -1);
+                const size_t xmn = step_from(g, xm, st.c[nu], nu, -1);  // x - mu - nu
+                AH acc = load_ah(A, g.V, p, st.s);
+                ah_axpy(acc, 1.f, conj_by(u1, load_ah(A, g.V, p, xm)));
+                const M3 u2 = load_link(hi, g.V, nu, xn);  // U_nu(x-nu)
+                ah_axpy(acc, 1.f, conj_by(u2, load_ah(A, g.V, p, xn)));
+                const M3 c = mul(load_link(hi, g.V, mu, xmn), u2);  // U_mu(x-mu-nu) U_nu(x-nu)
+                ah_axpy(acc, 1.f, conj_by(c, load_ah(A, g.V, p, xmn)));
+                AH r = ah_zero();
+                ah_axpy(r, 0.25f, acc);
+                f[p] = r;
+            }
+        }
+        float ef = 0.f;
+#pragma unroll
+        for (int p = 0; p < 6; ++p) ef += ah_dot(f[p], f[p]);
+        // planes: 0 xy, 1 xz, 2 xt, 3 yz, 4 yt, 5 zt
+        const float qf = (ah_dot(f[0], f[5]) - ah_dot(f[1], f[4]) + ah_dot(f[2], f[3])) *
+                         (float)(1.0 / (4.0 * 3.14159265358979323846 * 3.14159265358979323846));
+        e = ef;
+        q = qf;
+        if (e_site) e_site[st.s] = ef;
+        if (q_site) q_site[st.s] = qf;
+    }
+    block_sum2<kBS>(e, q, part_e + blockIdx.x, part_q + blockIdx.x);
+}
+
+// One block: sums the per-block partials in a fixed order and writes one observable record.
+constexpr int kRed = 256;
+__global__ void __launch_bounds__(kRed) reduce_kernel(int nblocks, const double* __restrict__ part_retr,
+                                                      const float* __restrict__ part_min, const double* __restrict__ part_e,
+                                                      const double* __restrict__ part_q, double t, double V,
+                                                      FlowObsDev* __restrict__ out) {
+    double r = 0, e = 0, q = 0;
+    float m = 3.0f;
+    for (int i = threadIdx.x; i < nblocks; i += kRed) {
+        r += part_retr[i];
+        e += part_e[i];
+        q += part_q[i];
+        m = fminf(m, part_min[i]);
+    }
+    __shared__ double sr[kRed], se[kRed], sq[kRed];
+    __shared__ float sm[kRed];
+    sr[threadIdx.x] = r;
+    se[threadIdx.x] = e;
+    sq[threadIdx.x] = q;
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = kRed / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sr[threadIdx.x] += sr[threadIdx.x + w];
+            se[threadIdx.x] += se[threadIdx.x + w];
+            sq[threadIdx.x] += sq[threadIdx.x + w];
+            sm[threadIdx.x] = fminf(sm[threadIdx.x], sm[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out->t = t;
+        out->e_plaq = 2.0 * (18.0 * V - sr[0]) / V;  // 2 sum_{6 planes} (3 - Re tr P), site average
+        out->e_clover = se[0] / V;
+        out->q_clover = sq[0];
+        out->plaq_min = (double)sm[0] / 3.0;
+        out->plaq_mean = sr[0] / (18.0 * V);
+    }
+}
+
+// external complex128 U[mu][site][a][b] <-> float-float pairs [mu][ab][site]
+__global__ void split_kernel(const double2* __restrict__ U, float2* __restrict__ hi, float2* __restrict__ lo, size_t V,
+                             int mu) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 9 * V) return;
+    const size_t s = i / 9;
+    const int k = (int)(i - s * 9);
+    const double2 u = U[i];
+    const float hx = (float)u.x, hy = (float)u.y;
+    const size_t o = ((size_t)mu * 9 + k) * V + s;
+    hi[o] = make_float2(hx, hy);
+    lo[o] = make_float2((float)(u.x - (double)hx), (float)(u.y - (double)hy));
+}
+
+__global__ void join_kernel(const float2* __restrict__ hi, const float2* __restrict__ lo, double2* __restrict__ U, size_t V,
+                            int mu) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 9 * V) return;
+    const size_t s = i / 9;
+    const int k = (int)(i - s * 9);
+    const size_t o = ((size_t)mu * 9 + k) * V + s;
+    const float2 h = hi[o], l = lo[o];
+    U[i] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+}
+
+}  // namespace
+
+size_t grid_blocks(const FlowGeom& g) { return (g.V + kBS - 1) / kBS; }
+
+cudaError_t launch_plaq(const FlowGeom& g, const float2* hi, float4* A, double* part_retr, float* part_min, bool measure,
+                        cudaStream_t st) {
+    const dim3 grid((unsigned)grid_blocks(g));
+    if (measure)
+        plaq_kernel<true><<<grid, kBS, 0, st>>>(g, hi, A, part_retr, part_min);
+    else
+        plaq_kernel<false><<<grid, kBS, 0, st>>>(g, hi, A, part_retr, part_min);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(const FlowGeom& g, int stage, const float2* hi, const float2* lo, float2* hi_out,
+                          float2* lo_out, const float4* A, float4* K, float eps, cudaStream_t st) {
+    const dim3 grid((unsigned)grid_blocks(g));
+    if (stage == 0)
+        update_kernel<0><<<grid, kBS, 0, st>>>(g, hi, lo, hi_out, lo_out, A, K, eps);
+    else if (stage == 1)
+        update_kernel<1><<<grid, kBS, 0, st>>>(g, hi, lo, hi_out, lo_out, A, K, eps);
+    else
+        update_kernel<2><<<grid, kBS, 0, st>>>(g, hi, lo, hi_out, lo_out, A, K, eps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clover(const FlowGeom& g, const float2* hi, const float4* A, double* part_e, double* part_q,
+                          float* e_site, float* q_site, cudaStream_t st) {
+    clover_kernel<<<(unsigned)grid_blocks(g), kBS, 0, st>>>(g, hi, A, part_e, part_q, e_site, q_site);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const FlowGeom& g, const double* part_retr, const float* part_min, const double* part_e,
+                          const double* part_q, double t, FlowObsDev* out, cudaStream_t st) {
+    reduce_kernel<<<1, kRed, 0, st>>>((int)grid_blocks(g), part_retr, part_min, part_e, part_q, t, (double)g.V, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split(const double2* U, float2* hi, float2* lo, size_t V, int mu, cudaStream_t st) {
+    const size_t n = 9 * V;
+    split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, hi, lo, V, mu);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_join(const float2* hi, const float2* lo, double2* U, size_t V, int mu, cudaStream_t st) {
+    const size_t n = 9 * V;
+    join_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(hi, lo, U, V, mu);
+    return cudaGetLastError();
+}
+
+}  // namespace flow
+}  // namespace odwf
