@@ -615,7 +615,7 @@ def run_flow(args, world, rank, local):
                        "step": "%d Runge-Kutta steps + one measurement" % FLOW_SEGMENT,
                        "gauge": "U = exp(0.2 i H), H Gaussian traceless Hermitian (seed 3)",
                        "site_steps_per_s": round(value * V, 1),
-                       "l2": "not flushed: the flow's working set (%.1f GB) exceeds L2" % (1472 * V / 1e9),
+                       "l2": "not flushed: the flow's working set (%.1f GB) exceeds L2" % (1088 * V / 1e9),
                        "parallelism": "replicas only" if world > 1 else "single GPU",
                        "observables": [{k: (round(v, 8) if isinstance(v, float) else v) for k, v in o.items()}
                                        for o in (obs[0], obs[-1])]},

@@ -19,10 +19,12 @@
  *   F          (Q - Q^+)/(8i), made traceless, Q the sum of the four plaquette loops at x.
  *   E(x)       e_clover: sum_{mu<nu} tr F_{mu nu}(x)^2;  e_plaq: 2 sum_{mu<nu} Re tr(1 - P_{mu nu}(x)).
  *
- * Precision: the links are held as pairs of FP32 numbers (hi + lo, about 48 significant bits);
- * the force, the exponential and the observables are computed in FP32 and every lattice sum is
- * accumulated in FP64.  A flow of n steps agrees with an FP64 integration to about
- * 1e-7 * n * eps * max|Z| in each link entry.
+ * Precision: the links are held as pairs of FP32 numbers (hi + lo, about 48 significant bits)
+ * of their first two rows; the third row of an SU(3) matrix is conj(row0 x row1) and is rebuilt
+ * where it is needed.  The force, the exponential and the observables are computed in FP32 and
+ * every lattice sum is accumulated in FP64.  A flow of n steps agrees with an FP64 integration to
+ * within n * eps * max|Z| * 64 * 2^-24 in each link entry (FP32 rounding of the force and of the
+ * stage increments).
  *
  * Conventions as in odwf.h: the gauge field is complex128 U[mu][t][z][y][x][a][b]; pointers may
  * be host or device memory (the library detects which); calls that return observables to the
@@ -55,7 +57,7 @@ typedef struct {
 
 /*
  * Create a flow object for a periodic lattice dims = {Lx, Ly, Lz, Lt}, every extent >= 2 (no
- * parity requirement).  Allocates its device memory at once: 1472 bytes per site (two buffers of
+ * parity requirement).  Allocates its device memory at once: 1088 bytes per site (two buffers of
  * float-float links, the six plaquette projections and the Runge-Kutta carry) plus per-block
  * partial sums.  ODWF_EINVAL on bad sizes, ODWF_ENOMEM when the allocation fails.
  */
@@ -64,7 +66,8 @@ int odwf_flow_create(const int32_t dims[4], odwf_flow** out);
 /* Free the object and its device memory. */
 int odwf_flow_destroy(odwf_flow* f);
 
-/* Load the gauge field U (host or device, complex128, V * 36 entries) as the flow's field at t = 0. */
+/* Load the gauge field U (host or device, complex128, V * 36 entries) as the flow's field at t = 0.
+ * U must be in SU(3): the third row of each link is not read but rebuilt from the first two. */
 int odwf_flow_set_gauge(odwf_flow* f, const void* U, void* stream);
 
 /* Write the current (flowed) field to U (host or device, complex128, layout above). */

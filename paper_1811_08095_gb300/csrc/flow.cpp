@@ -18,8 +18,8 @@ using odwf::flow::FlowObsDev;
 struct odwf_flow {
     int device = 0;
     FlowGeom g{};
-    float2* hi[2] = {nullptr, nullptr};
-    float2* lo[2] = {nullptr, nullptr};
+    float4* hi[2] = {nullptr, nullptr};  // first two rows of every link, [mu][3][V] float4 (hi + lo = the link)
+    float4* lo[2] = {nullptr, nullptr};
     int cur = 0;
     float4* A = nullptr;  // six plaquette projections, [plane][2][V]
     float4* K = nullptr;  // Runge-Kutta carry, [mu][2][V]
@@ -111,10 +111,10 @@ struct Timed {
     }
 };
 
-// bytes per site: links hi 288, lo 288 (per buffer), plaquette projections 192, carry 128
-constexpr double kPlaqBytes = 288 + 192;
-constexpr double kCloverBytes = 288 + 192;
-double update_bytes(int stage) { return 192 + 2 * 288 + 2 * 288 + (stage > 0 ? 128 : 0) + (stage < 2 ? 128 : 0); }
+// bytes per site: links hi 192, lo 192 (two rows, per buffer), plaquette projections 192, carry 128
+constexpr double kPlaqBytes = 192 + 192;
+constexpr double kCloverBytes = 192 + 192;
+double update_bytes(int stage) { return 192 + 2 * 192 + 2 * 192 + (stage > 0 ? 128 : 0) + (stage < 2 ? 128 : 0); }
 
 int launch_plaq_t(odwf_flow* f, bool measure, cudaStream_t st) {
     Timed t(measure ? "flow.plaq_measure" : "flow.plaq", kPlaqBytes * f->g.V, st);
@@ -133,7 +133,7 @@ int measure_into(odwf_flow* f, double t, int slot, float* e_site, float* q_site,
         FCK(fl::launch_clover(f->g, f->hi[f->cur], f->A, f->part_e, f->part_q, e_site, q_site, st));
     }
     {
-        Timed tm("flow.reduce", 28.0 * fl::grid_blocks(f->g), st);
+        Timed tm("flow.reduce", 12.0 * fl::plaq_blocks(f->g) + 16.0 * fl::clover_blocks(f->g), st);
         FCK(fl::launch_reduce(f->g, f->part_retr, f->part_min, f->part_e, f->part_q, t, f->obs_dev + slot, st));
     }
     return ODWF_OK;
@@ -174,18 +174,18 @@ int odwf_flow_create(const int32_t dims[4], odwf_flow** out) {
     }
     g.V = V;
     g.bt = dims[3] % 8 == 0 ? 8 : dims[3] % 4 == 0 ? 4 : dims[3] % 2 == 0 ? 2 : 1;
-    const size_t nb = odwf::flow::grid_blocks(g);
+    const size_t nbp = odwf::flow::plaq_blocks(g), nbc = odwf::flow::clover_blocks(g);
     int rc = 0;
     for (int b = 0; b < 2 && !rc; ++b) {
-        rc = alloc((void**)&f->hi[b], 36 * V * sizeof(float2), "links (hi)");
-        if (!rc) rc = alloc((void**)&f->lo[b], 36 * V * sizeof(float2), "links (lo)");
+        rc = alloc((void**)&f->hi[b], 12 * V * sizeof(float4), "links (hi)");
+        if (!rc) rc = alloc((void**)&f->lo[b], 12 * V * sizeof(float4), "links (lo)");
     }
     if (!rc) rc = alloc((void**)&f->A, 12 * V * sizeof(float4), "plaquette projections");
     if (!rc) rc = alloc((void**)&f->K, 8 * V * sizeof(float4), "Runge-Kutta carry");
-    if (!rc) rc = alloc((void**)&f->part_retr, nb * sizeof(double), "partial sums");
-    if (!rc) rc = alloc((void**)&f->part_min, nb * sizeof(float), "partial minima");
-    if (!rc) rc = alloc((void**)&f->part_e, nb * sizeof(double), "partial sums");
-    if (!rc) rc = alloc((void**)&f->part_q, nb * sizeof(double), "partial sums");
+    if (!rc) rc = alloc((void**)&f->part_retr, nbp * sizeof(double), "partial sums");
+    if (!rc) rc = alloc((void**)&f->part_min, nbp * sizeof(float), "partial minima");
+    if (!rc) rc = alloc((void**)&f->part_e, nbc * sizeof(double), "partial sums");
+    if (!rc) rc = alloc((void**)&f->part_q, nbc * sizeof(double), "partial sums");
     if (!rc) rc = ensure_obs(f, 64);
     if (rc) {
         release(f);
