@@ -69,7 +69,9 @@ enum {
     ODWF_EBUSY = 10       /* serving: the queue is full (serve_set_policy); the request was not taken */
 };
 
-typedef enum { ODWF_F64 = 0, ODWF_F32 = 1, ODWF_F16 = 2, ODWF_BF16 = 3 } odwf_prec;
+/* ODWF_FF: float-float, each real the unevaluated sum of two FP32 numbers (about 48 bits),
+ * arithmetic built from FP32 operations: the reliable updates of the mixed-precision CG. */
+typedef enum { ODWF_F64 = 0, ODWF_F32 = 1, ODWF_F16 = 2, ODWF_BF16 = 3, ODWF_FF = 4 } odwf_prec;
 
 enum { ODWF_MODE_FULL = 0, ODWF_MODE_SCHUR_EVEN = 1 };
 
@@ -80,6 +82,8 @@ enum {
 };
 
 enum { ODWF_OMEGA_SHIFTED_R5 = 0, ODWF_OMEGA_PLAIN = 1 };
+
+enum { ODWF_UPDATES_AUTO = 0, ODWF_UPDATES_F64 = 1, ODWF_UPDATES_FF = 2 };
 
 typedef struct {
     int32_t dims[4];        /* Lx, Ly, Lz, Lt */
@@ -92,7 +96,8 @@ typedef struct {
     double tol;         /* target true relative residual ||b - A x|| / ||b|| (e.g. 1e-10) */
     int32_t max_iter;   /* cap on inner CG iterations (summed over restarts) */
     int32_t prec;       /* ODWF_F64: plain FP64 CG; ODWF_F32/F16/BF16: mixed precision with that
-                           storage for the inner operator fields, FP32 arithmetic, FP64 reliable updates */
+                           storage for the inner operator fields, FP32 arithmetic, reliable updates
+                           (true residual b - A x) in FP64 or float-float (update_arith) */
     double delta;       /* reliable-update trigger: recompute the FP64 residual when the inner
                            residual drops below delta x its largest value since the last update
                            (<= 0 selects 0.01) */
@@ -103,12 +108,22 @@ typedef struct {
     int32_t link_prec;  /* mixed inner links: 0 or ODWF_F32 = FP32; ODWF_F16 = FP16 with 12 reals
                            (24 bytes per link, no scale: SU(3) entries have modulus <= 1; needs
                            Ns = 8 or 16 and link_recon 0 or 12) */
+    int32_t update_arith; /* mixed: arithmetic of the reliable updates (true residual b - A x) and of
+                           the accumulated solution.  ODWF_UPDATES_AUTO (0): float-float for a solve
+                           of one system, FP64 for batches; ODWF_UPDATES_F64: FP64;
+                           ODWF_UPDATES_FF: float-float (pairs of FP32, about 48 bits, on the FP32
+                           pipe).  Both resolve the true residual far below 1e-10.  Float-float is
+                           faster when the update is on the critical path (one system); in a batch
+                           the FP64 pipe runs beside the FP32-bound iterations of the other systems,
+                           where float-float competes with them for the FP32 pipe.  Full-lattice
+                           systems (FULL_NORMAL, FULL_DIRAC) always update in FP64. */
 } odwf_solve_params;
 
 typedef struct {
     int32_t iters;          /* inner CG iterations */
     int32_t n_reliable;     /* FP64 residual recomputations */
-    double true_resid;      /* final ||b - A x|| / ||b||, recomputed in FP64 on the GPU */
+    double true_resid;      /* final ||b - A x|| / ||b||, recomputed on the GPU (FP64, or float-float
+                               for mixed solves that update in float-float) */
     double time_ms;         /* wall time of the solve inside the library */
     int32_t status;         /* ODWF_OK / ODWF_ENOCONV / ODWF_EBREAKDOWN for this system */
     int32_t reserved;
@@ -176,6 +191,8 @@ int odwf_apply_normal(odwf_handle* h, void* out, const void* in, int system, voi
  * site), the four hops run in FP32 with FP32 links of `link_recon` (12 or 18) reals, and
  * every intermediate field is stored in `prec`.  Even-site fields, as odwf_apply_normal.
  * This is the operator the inner CG iterates with; it is exposed for accuracy checks.
+ * prec = ODWF_FF gives the reliable updates' operator instead: float-float fields, links and
+ * arithmetic throughout (link_recon is ignored).
  */
 int odwf_apply_normal_prec(odwf_handle* h, void* out, const void* in, int prec, int link_recon, void* stream);
 

@@ -22,7 +22,7 @@ __all__ = ["Handle", "Server", "Flow", "odwf_flow_t0", "odwf_zolotarev_omega", "
            "ODWF_SYS_FULL_NORMAL", "ODWF_SYS_FULL_DIRAC", "ODWF_OMEGA_SHIFTED_R5", "ODWF_OMEGA_PLAIN",
            "load", "lib_path"]
 
-PREC = {"f64": ODWF_F64, "f32": ODWF_F32, "f16": ODWF_F16, "bf16": ODWF_BF16}
+PREC = {"f64": ODWF_F64, "f32": ODWF_F32, "f16": ODWF_F16, "bf16": ODWF_BF16, "ff": _lib.ODWF_FF}
 
 
 def load(build_if_missing: bool = False):
@@ -132,7 +132,10 @@ def _lattice(dims, t_antiperiodic):
     return lat
 
 
-def _params(tol, max_iter, prec, delta, system, link_recon, mq, check_every, link_prec="f32"):
+UPDATES = {"auto": _lib.ODWF_UPDATES_AUTO, "f64": _lib.ODWF_UPDATES_F64, "ff": _lib.ODWF_UPDATES_FF}
+
+
+def _params(tol, max_iter, prec, delta, system, link_recon, mq, check_every, link_prec="f32", updates="auto"):
     p = _lib.odwf_solve_params()
     p.tol = float(tol)
     p.max_iter = int(max_iter)
@@ -143,6 +146,7 @@ def _params(tol, max_iter, prec, delta, system, link_recon, mq, check_every, lin
     p.mq = float("nan") if mq is None else float(mq)
     p.check_every = int(check_every)
     p.link_prec = PREC[link_prec] if isinstance(link_prec, str) else int(link_prec)
+    p.update_arith = UPDATES[updates] if isinstance(updates, str) else int(updates)
     return p
 
 
@@ -265,8 +269,9 @@ class Handle:
         return mres.value, corr, _stats_dict(st)
 
     def cg_solve(self, x, b, tol=1e-10, max_iter=100000, prec="f64", delta=0.01, system=ODWF_SYS_SCHUR_NORMAL,
-                 link_recon=12, mq=None, check_every=8, stream=None, raise_on_error=True, link_prec="f32"):
-        p = _params(tol, max_iter, prec, delta, system, link_recon, mq, check_every, link_prec)
+                 link_recon=12, mq=None, check_every=8, stream=None, raise_on_error=True, link_prec="f32",
+                 updates="auto"):
+        p = _params(tol, max_iter, prec, delta, system, link_recon, mq, check_every, link_prec, updates)
         st = _lib.odwf_solve_stats()
         rc = self._lib.odwf_cg_solve(self._h, ptr(x), ptr(b), ctypes.byref(p), ctypes.byref(st), stream_ptr(stream))
         if raise_on_error:
@@ -276,7 +281,8 @@ class Handle:
         return d
 
     def cg_solve_batched(self, xs, bs, mqs=None, tol=1e-10, max_iter=100000, prec="f64", delta=0.01,
-                         link_recon=12, check_every=8, stream=None, raise_on_error=True, link_prec="f32"):
+                         link_recon=12, check_every=8, stream=None, raise_on_error=True, link_prec="f32",
+                         updates="auto"):
         n = len(xs)
         assert len(bs) == n
         xa = (ctypes.c_void_p * n)(*[ptr(x).value for x in xs])
@@ -286,7 +292,8 @@ class Handle:
             mq_np = np.ascontiguousarray(mqs, dtype=np.float64)
             assert mq_np.shape == (n,)
             mq_arr = ptr(mq_np)
-        p = _params(tol, max_iter, prec, delta, ODWF_SYS_SCHUR_NORMAL, link_recon, None, check_every, link_prec)
+        p = _params(tol, max_iter, prec, delta, ODWF_SYS_SCHUR_NORMAL, link_recon, None, check_every, link_prec,
+                    updates)
         st = (_lib.odwf_solve_stats * n)()
         rc = self._lib.odwf_cg_solve_batched(self._h, n, ctypes.cast(xa, ctypes.c_void_p),
                                              ctypes.cast(ba, ctypes.c_void_p), mq_arr, ctypes.byref(p),

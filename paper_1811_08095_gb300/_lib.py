@@ -19,10 +19,11 @@ LIB_PATH = os.environ.get("ODWF_LIBRARY") or os.path.join(_HERE, "libodwf.so")
 
 ODWF_OK, ODWF_EINVAL, ODWF_ENOMEM, ODWF_ENOCONV, ODWF_EBREAKDOWN, ODWF_ETIMEOUT, ODWF_ECUDA, ODWF_PENDING, \
     ODWF_ENOTFOUND, ODWF_ECANCELED, ODWF_EBUSY = range(11)
-ODWF_F64, ODWF_F32, ODWF_F16, ODWF_BF16 = range(4)
+ODWF_F64, ODWF_F32, ODWF_F16, ODWF_BF16, ODWF_FF = range(5)
 ODWF_MODE_FULL, ODWF_MODE_SCHUR_EVEN = 0, 1
 ODWF_SYS_SCHUR_NORMAL, ODWF_SYS_FULL_NORMAL, ODWF_SYS_FULL_DIRAC = 0, 1, 2
 ODWF_OMEGA_SHIFTED_R5, ODWF_OMEGA_PLAIN = 0, 1
+ODWF_UPDATES_AUTO, ODWF_UPDATES_F64, ODWF_UPDATES_FF = 0, 1, 2
 
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOCONV", 4: "EBREAKDOWN", 5: "ETIMEOUT", 6: "ECUDA",
                 7: "PENDING", 8: "ENOTFOUND", 9: "ECANCELED", 10: "EBUSY"}
@@ -35,7 +36,8 @@ class odwf_lattice(ctypes.Structure):
 class odwf_solve_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("delta", ctypes.c_double), ("system", ctypes.c_int32), ("link_recon", ctypes.c_int32),
-                ("mq", ctypes.c_double), ("check_every", ctypes.c_int32), ("link_prec", ctypes.c_int32)]
+                ("mq", ctypes.c_double), ("check_every", ctypes.c_int32), ("link_prec", ctypes.c_int32),
+                ("update_arith", ctypes.c_int32)]
 
 
 class odwf_solve_stats(ctypes.Structure):

@@ -39,6 +39,15 @@ HopParams<double> BatchCG::params<double>(int p_out) const {
 }
 
 template <>
+HopParams<ff> BatchCG::params<ff>(int p_out) const {
+    auto P = E->hop_params<ff>(p_out, r_dev);
+    P.st = st;
+    P.partials = partials;
+    P.counters = counters;
+    return P;
+}
+
+template <>
 HopParams<float> BatchCG::params<float>(int p_out) const {
     auto P = E->hop_params<float>(p_out, r_dev);
     P.links = v2 ? E->links_site[(int)lk] : E->links_of(lk);
@@ -53,15 +62,20 @@ int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStr
     cap = capacity;
     mixed = prm.prec != ODWF_F64;
     low = (Sp)prm.prec;
+    // float-float updates for one system (the update is on its critical path); FP64 for batches,
+    // whose FP64 updates overlap the other systems' FP32-bound iterations
+    const bool ffu = prm.update_arith == ODWF_UPDATES_FF || (prm.update_arith == ODWF_UPDATES_AUTO && cap == 1);
+    fsp = mixed && ffu ? Sp::FF : Sp::F64;
     lk = link_format(prm);
     delta = prm.delta > 0 ? prm.delta : 0.01;
     tol = prm.tol;
     max_iter = prm.max_iter;
     int rc = 0;
     const int nrb = mixed ? 1 : cap;  // mixed: R64 and B64 are shared by all systems
-    if ((rc = E->alloc_half("cg.X64", Sp::F64, cap, &X64)) || (rc = E->alloc_half("cg.R64", Sp::F64, nrb, &R64)) ||
-        (rc = E->alloc_half("cg.B64", Sp::F64, nrb, &B64)))
+    if ((rc = E->alloc_half("cg.X64", fsp, cap, &X64)) || (rc = E->alloc_half("cg.R64", fsp, nrb, &R64)) ||
+        (rc = E->alloc_half("cg.B64", fsp, nrb, &B64)))
         return rc;
+    if (fsp == Sp::FF && (rc = E->ensure_links(Lk::FF18, s))) return rc;
     if (!mixed) {
         if ((rc = E->alloc_half("cg.P64", Sp::F64, cap, &P64)) || (rc = E->alloc_half("cg.T64", Sp::F64, cap, &T64)) ||
             (rc = E->alloc_half("cg.A64", Sp::F64, cap, &A64)) || (rc = E->alloc_half("cg.C64", Sp::F64, cap, &C64)))
@@ -71,7 +85,7 @@ int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStr
         if ((rc = E->alloc_half("cg.Rin", Sp::F32, cap, &Rin)) || (rc = E->alloc_half("cg.Xin", Sp::F32, cap, &Xin)) ||
             (rc = E->alloc_half(tag + ".P", low, cap, &Pl)) || (rc = E->alloc_half(tag + ".T", low, cap, &Tl)) ||
             (rc = E->alloc_half(tag + ".A", low, cap, &Al)) || (rc = E->alloc_half(tag + ".C", low, cap, &Cl)) ||
-            (rc = E->alloc_half("cg.A1", Sp::F64, 1, &A1)) || (rc = E->alloc_half("cg.C1", Sp::F64, 1, &C1)))
+            (rc = E->alloc_half("cg.A1", fsp, 1, &A1)) || (rc = E->alloc_half("cg.C1", fsp, 1, &C1)))
             return rc;
         if ((rc = E->ensure_links(lk, s))) return rc;
         v2 = hop2_supported(E->ns, low, E->vh());
@@ -138,10 +152,11 @@ int BatchCG::init(Engine* e, int capacity, const odwf_solve_params& prm, cudaStr
     pcls[4] = prof_class(pre + ".P_update", n5 * (acc + 2 * sp), 0.0);
     }
     const double l64 = 8.0 * (double)E->vh() * 144.0;
-    pcls_rel[0] = prof_class("f64.reliable.K1_minv", n5 * 2 * 192.0, l64);
-    pcls_rel[1] = prof_class("f64.reliable.K2_schur_mdinv", n5 * 3 * 192.0, l64);
-    pcls_rel[2] = prof_class("f64.reliable.K3_dag_minvdag", n5 * 2 * 192.0, l64);
-    pcls_rel[3] = prof_class("f64.reliable.K4_resid", n5 * 4 * 192.0, l64);
+    const std::string rn = fsp == Sp::FF ? "ff.reliable." : "f64.reliable.";
+    pcls_rel[0] = prof_class(rn + "K1_minv", n5 * 2 * 192.0, l64);
+    pcls_rel[1] = prof_class(rn + "K2_schur_mdinv", n5 * 3 * 192.0, l64);
+    pcls_rel[2] = prof_class(rn + "K3_dag_minvdag", n5 * 2 * 192.0, l64);
+    pcls_rel[3] = prof_class(rn + "K4_resid", n5 * 4 * 192.0, l64);
     return ODWF_OK;
 }
 
@@ -180,7 +195,7 @@ int BatchCG::order_after(cudaStream_t first, cudaStream_t then) {
 }
 
 int BatchCG::load_b(int slot, cudaStream_t s) {
-    if (mixed && bsrc[slot]) ODWF_CK(launch_pack(Sp::F64, bsrc[slot], B64.ref_sys(0), E->g, 0, E->ns, 1, s));
+    if (mixed && bsrc[slot]) ODWF_CK(launch_pack(fsp, bsrc[slot], B64.ref_sys(0), E->g, 0, E->ns, 1, s));
     return ODWF_OK;
 }
 
@@ -222,20 +237,20 @@ int BatchCG::admit_internal(int slot, cudaStream_t s, double tol_slot, int max_i
     ODWF_CK(cudaMemcpyAsync(st + slot, stage, sizeof(SysState), cudaMemcpyHostToDevice, s));
     // ||b||^2 -> state, then rr = bb, status running
     const FieldRef B = Bref();
-    ODWF_CK(launch_vec(Sp::F64, Sp::F64, B, B, n5, ns, 3, 0.0, st, 0, 0, partials, counters, slot, 1, s));
+    ODWF_CK(launch_vec(fsp, fsp, B, B, n5, ns, 3, 0.0, st, 0, 0, partials, counters, slot, 1, s));
     ODWF_CK(launch_state(st + slot, 1, 0, tl * tl, s));
-    ODWF_CK(launch_vec(Sp::F64, Sp::F64, X64.ref(), X64.ref(), n5, ns, 5, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
+    ODWF_CK(launch_vec(fsp, fsp, X64.ref(), X64.ref(), n5, ns, 5, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
     if (!mixed) {
         ODWF_CK(launch_vec(Sp::F64, Sp::F64, B, R64.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
         ODWF_CK(launch_vec(Sp::F64, Sp::F64, B, P64.ref(), n5, ns, 0, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
     } else {
-        ODWF_CK(launch_vec(Sp::F64, Sp::F32, B, Rin.ref(), n5, ns, 6, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
+        ODWF_CK(launch_vec(fsp, Sp::F32, B, Rin.ref(), n5, ns, 6, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
         ODWF_CK(launch_vec(Sp::F32, Sp::F32, Xin.ref(), Xin.ref(), n5, ns, 5, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
         if (v2) {
             ODWF_CK(launch_p_update2(low, ns, Rin.ref(), Pl.ref(), Chil.ref(), E->vh(), 0, E->cf32, r_dev, st, 0, 0,
                                      slot, 1, nullptr, s));
         } else {
-            ODWF_CK(launch_vec(Sp::F64, low, B, Pl.ref(), n5, ns, 6, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
+            ODWF_CK(launch_vec(fsp, low, B, Pl.ref(), n5, ns, 6, 0.0, st, 0, 0, nullptr, nullptr, slot, 1, s));
         }
     }
     active[slot] = 1;
@@ -499,7 +514,41 @@ int BatchCG::resume(cudaStream_t s, bool block) {
 
 // R[slot] = B[slot] - S^dag S X[slot] in FP64, |R|^2 -> st[slot].sum (mixed: R and B are the
 // shared buffers, B loaded with the slot's right-hand side)
+// The reliable update's r = b - S^dag S x in float-float arithmetic (fields, links and
+// coefficients as FP32 pairs): the same launch sequence as the FP64 one below.
+int BatchCG::ff_residual(int slot, cudaStream_t s) {
+    const FieldRef t = Rref(), a = A1.ref_shared(), c = C1.ref_shared();
+    const size_t vh = E->vh();
+    ODWF_CK(launch_m5_ff(X64.ref(), c, vh, E->ns, r_dev, slot, 1, 4, E->cfff, s));
+    auto P = params<ff>(1);
+    P.sys_base = slot;
+    P.preshifted = 1;
+    P.in = c;
+    P.out = t;
+    { auto pb_ = prof_begin(pcls_rel[0], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_ff(P, Epi::MINV, 1, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+    ODWF_CK(launch_m5_ff(t, c, vh, E->ns, r_dev, slot, 1, 4, E->cfff, s));
+    P.p_out = 0;
+    P.in = c;
+    P.z = X64.ref();
+    P.out = a;
+    { auto pb_ = prof_begin(pcls_rel[1], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_ff(P, Epi::SCHUR_MDINV, 1, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+    P.preshifted = 0;
+    P.p_out = 1;
+    P.in = a;
+    P.z = FieldRef{};
+    P.out = c;
+    { auto pb_ = prof_begin(pcls_rel[2], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_ff(P, Epi::D_MINVDAG, 1, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+    P.p_out = 0;
+    P.in = c;
+    P.z = a;
+    P.b = Bref();
+    P.out = Rref();
+    { auto pb_ = prof_begin(pcls_rel[3], s); P.prof_count = pb_.dev_count; ODWF_CK(launch_hop_ff(P, Epi::D_NORMAL_RESID, 1, s)); prof_end(pb_, s); P.prof_count = nullptr; }
+    return ODWF_OK;
+}
+
 int BatchCG::fp64_residual(int slot, cudaStream_t s) {
+    if (fsp == Sp::FF) return ff_residual(slot, s);
     const HalfField& X = X64;
     FieldRef t, a, c;
     if (mixed) {
@@ -552,14 +601,14 @@ int BatchCG::service(cudaStream_t s) {
         ODWF_CK(cudaStreamWaitEvent(s_rel, ev_rel[i], 0));
         cudaStream_t r = s_rel;
         if (mixed)  // X64 += rscale x_in, x_in = 0
-            ODWF_CK(launch_vec(Sp::F32, Sp::F64, Xin.ref(), X64.ref(), n5, E->ns, 7, 0.0, st, 0, 0, nullptr, nullptr,
+            ODWF_CK(launch_vec(Sp::F32, fsp, Xin.ref(), X64.ref(), n5, E->ns, 7, 0.0, st, 0, 0, nullptr, nullptr,
                                i, 1, r));
         int rc = load_b(i, r);
         if (!rc) rc = fp64_residual(i, r);
         if (rc) return rc;
         ODWF_CK(launch_state(st + i, 1, 1, tol * tol, r));  // done / max-iter / kRestarting
         if (mixed) {
-            ODWF_CK(launch_vec(Sp::F64, Sp::F32, Rref(), Rin.ref(), n5, E->ns, 6, 0.0, st, 1, kRestarting, nullptr,
+            ODWF_CK(launch_vec(fsp, Sp::F32, Rref(), Rin.ref(), n5, E->ns, 6, 0.0, st, 1, kRestarting, nullptr,
                                nullptr, i, 1, r));
             if (v2) {
                 ODWF_CK(launch_p_update2(low, E->ns, Rin.ref(), Pl.ref(), Chil.ref(), E->vh(), 1, E->cf32, r_dev, st,
@@ -593,7 +642,7 @@ int BatchCG::finalize(int slot, double2* x_ext, cudaStream_t s, double* true_res
         // breakdown (or an unfinished slot): fold and recompute the true residual
         int rc = ODWF_OK;
         if (mixed) {
-            ODWF_CK(launch_vec(Sp::F32, Sp::F64, Xin.ref(), X64.ref(), E->sites5(), E->ns, 7, 0.0, st, 0, 0, nullptr,
+            ODWF_CK(launch_vec(Sp::F32, fsp, Xin.ref(), X64.ref(), E->sites5(), E->ns, 7, 0.0, st, 0, 0, nullptr,
                                nullptr, slot, 1, s));
             rc = order_after(s_rel, s);  // the shared FP64 buffers are free
             if (!rc) rc = load_b(slot, s);
@@ -602,7 +651,7 @@ int BatchCG::finalize(int slot, double2* x_ext, cudaStream_t s, double* true_res
         if (!rc && mixed) rc = order_after(s, s_rel);
         if (rc) return rc;
     }
-    if (x_ext) ODWF_CK(launch_unpack(Sp::F64, X64.ref_sys(slot), x_ext, E->g, 0, E->ns, 1, s));
+    if (x_ext) ODWF_CK(launch_unpack(fsp, X64.ref_sys(slot), x_ext, E->g, 0, E->ns, 1, s));
     ODWF_CK(cudaMemcpyAsync(st_host + slot, st + slot, sizeof(SysState), cudaMemcpyDeviceToHost, s));
     ODWF_CK(cudaStreamSynchronize(s));
     const SysState& S = st_host[slot];

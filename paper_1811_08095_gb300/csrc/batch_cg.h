@@ -42,6 +42,7 @@ struct BatchCG {
     int cap = 0;
     bool mixed = false;
     Sp low = Sp::F16;
+    Sp fsp = Sp::F64;  // X64, R64, B64 and the reliable-update temporaries: F64, or FF (float-float) when mixed
     Lk lk = Lk::F12;
     double delta = 0.1;
     double tol = 1e-10;
@@ -117,6 +118,7 @@ struct BatchCG {
    private:
     template <class R>
     HopParams<R> params(int p_out) const;
+    int ff_residual(int slot, cudaStream_t s);
     int fp64_residual(int slot, cudaStream_t s);
     int launch_iterations(int k, int lo, int n, cudaStream_t s);
     void drop_graphs();

@@ -70,6 +70,7 @@ int Engine::mixed_cg_step(int prec, int recon, int link_prec, double mq_step, co
     prm.system = ODWF_SYS_SCHUR_NORMAL;
     prm.link_recon = recon;
     prm.link_prec = link_prec;
+    prm.update_arith = ODWF_UPDATES_F64;  // no reliable update runs here
     BatchCG bc;
     int rc = bc.init(this, 1, prm, st, 0);
     if (rc) return rc;
@@ -132,6 +133,7 @@ int Engine::time_kernel(int kind, int prec, int recon, int link_prec, int nsys, 
     prm.delta = 0.01;
     prm.link_recon = recon;
     prm.link_prec = link_prec;
+    prm.update_arith = ODWF_UPDATES_F64;  // no reliable update runs here
     BatchCG bc;
     int rc = bc.init(this, nsys, prm, st, 0);
     if (rc) return rc;

@@ -51,6 +51,7 @@ Engine::~Engine() {
     if (links_f18) cudaFree(links_f18);
     if (links_f12) cudaFree(links_f12);
     if (links_h12) cudaFree(links_h12);
+    if (links_ff18) cudaFree(links_ff18);
     for (void* p : links_site)
         if (p) cudaFree(p);
     if (nbr) cudaFree(nbr);
@@ -94,6 +95,11 @@ int Engine::init(const odwf_lattice* l, int Ns, double m0_, double mq_, const do
         cf32.d[s] = (float)cf64.d[s];
         cf32.e[s] = (float)cf64.e[s];
         cf32.inv_d[s] = (float)cf64.inv_d[s];
+        cfff.rho[s] = ff(cf64.rho[s]);
+        cfff.sigma[s] = ff(cf64.sigma[s]);
+        cfff.d[s] = ff(cf64.d[s]);
+        cfff.e[s] = ff(cf64.e[s]);
+        cfff.inv_d[s] = ff(cf64.inv_d[s]);
     }
     ODWF_CK(cudaGetDevice(&device));
     int rc = 0;
@@ -124,6 +130,7 @@ int Engine::bounds_status(cudaStream_t st) {
 size_t Engine::half_bytes(Sp sp) const {
     switch (sp) {
         case Sp::F64: return sites5() * 192;
+        case Sp::FF: return sites5() * 192;
         case Sp::F32: return sites5() * 96;
         default: return sites5() * 48;
     }
@@ -197,7 +204,7 @@ int Engine::set_gauge(const void* U, cudaStream_t st) {
     if (!links_d18) ODWF_CK(cudaMalloc(&links_d18, nl * 144));
     ODWF_CK(launch_pack_links(Ud, links_d18, nullptr, nullptr, g, st));
     // FP32 copies are derived from the FP64 ones on first use (ensure_links)
-    have_f12 = have_f18 = have_h12 = false;
+    have_f12 = have_f18 = have_h12 = have_ff18 = false;
     for (bool& b : have_site) b = false;
     if (!is_device_ptr(U)) {
         ODWF_CK(cudaStreamSynchronize(st));
@@ -226,6 +233,10 @@ int Engine::ensure_links(Lk lk, cudaStream_t st) {
         if (!links_f18) ODWF_CK(cudaMalloc(&links_f18, nl * 80));
         ODWF_CK(launch_links_from_d18(links_d18, links_f18, nullptr, nl, st));
         have_f18 = true;
+    } else if (lk == Lk::FF18 && !have_ff18) {
+        if (!links_ff18) ODWF_CK(cudaMalloc(&links_ff18, nl * 144));
+        ODWF_CK(launch_links_ff18_from_d18(links_d18, links_ff18, nl, st));
+        have_ff18 = true;
     } else if (lk == Lk::H12 && !have_h12) {
         if (!links_h12) ODWF_CK(cudaMalloc(&links_h12, nl * 24));
         ODWF_CK(launch_links_h12_from_d18(links_d18, links_h12, nl, st));
@@ -257,6 +268,21 @@ HopParams<double> Engine::hop_params<double>(int p_out, const double* r_dev) con
     P.links = links_d18;
     P.r_sys = r_dev;
     P.cf = cf64;
+    P.bounds_flag = bounds_flag;
+    return P;
+}
+
+template <>
+HopParams<ff> Engine::hop_params<ff>(int p_out, const double* r_dev) const {
+    HopParams<ff> P;
+    std::memset(&P, 0, sizeof(P));
+    P.g = g;
+    P.ns = ns;
+    P.lg_ns = lg_ns;
+    P.p_out = p_out;
+    P.links = links_ff18;
+    P.r_sys = r_dev;
+    P.cf = cfff;
     P.bounds_flag = bounds_flag;
     return P;
 }
@@ -430,11 +456,58 @@ int Engine::apply_normal(void* out, const void* in, int system, cudaStream_t st)
     return ODWF_OK;
 }
 
+// S^dag S in float-float arithmetic with float-float fields and links: the operator of the
+// mixed-precision CG's reliable updates.
+int Engine::apply_ff_normal(void* out, const void* in, cudaStream_t st) {
+    if (!out || !in) return fail(ODWF_EINVAL, "apply_normal_prec: null field");
+    const size_t eb = ext_bytes(ODWF_MODE_SCHUR_EVEN);
+    int rc = 0;
+    const double2* din = nullptr;
+    if ((rc = stage_in(this, in, eb, "ext.in", st, &din))) return rc;
+    const bool out_dev = is_device_ptr(out);
+    double2* dout = out_dev ? (double2*)out : (double2*)get_ws("ext.out", eb, &rc);
+    if (rc) return rc;
+    const double* rd = (const double*)ws["r_handle"].p;
+    HalfField X, Y, T, A, C;
+    if ((rc = alloc_half("ff.X", Sp::FF, 1, &X)) || (rc = alloc_half("ff.Y", Sp::FF, 1, &Y)) ||
+        (rc = alloc_half("ff.T", Sp::FF, 1, &T)) || (rc = alloc_half("ff.A", Sp::FF, 1, &A)) ||
+        (rc = alloc_half("ff.C", Sp::FF, 1, &C)))
+        return rc;
+    if ((rc = ensure_links(Lk::FF18, st))) return rc;
+    ODWF_CK(launch_pack(Sp::FF, din, X.ref_sys(0), g, 0, ns, 1, st));
+    auto P = hop_params<ff>(1, rd);
+    P.in = X.ref_sys(0);
+    P.out = T.ref_sys(0);
+    ODWF_CK(launch_hop_ff(P, Epi::MINV, 1, st));
+    P.p_out = 0;
+    P.in = T.ref_sys(0);
+    P.z = X.ref_sys(0);
+    P.out = A.ref_sys(0);
+    ODWF_CK(launch_hop_ff(P, Epi::SCHUR_MDINV, 1, st));
+    P.p_out = 1;
+    P.in = A.ref_sys(0);
+    P.z = FieldRef{};
+    P.out = C.ref_sys(0);
+    ODWF_CK(launch_hop_ff(P, Epi::D_MINVDAG, 1, st));
+    P.p_out = 0;
+    P.in = C.ref_sys(0);
+    P.z = A.ref_sys(0);
+    P.out = Y.ref_sys(0);
+    ODWF_CK(launch_hop_ff(P, Epi::D_NORMAL, 1, st));
+    ODWF_CK(launch_unpack(Sp::FF, Y.ref_sys(0), dout, g, 0, ns, 1, st));
+    if (!out_dev) {
+        ODWF_CK(cudaMemcpyAsync(out, dout, eb, cudaMemcpyDeviceToHost, st));
+        ODWF_CK(cudaStreamSynchronize(st));
+    }
+    return ODWF_OK;
+}
+
 int Engine::apply_low_normal(void* out, const void* in, int prec, int recon, cudaStream_t st) {
     if (!gauge_set) return fail(ODWF_EINVAL, "apply_normal_prec: gauge field not set");
     if (!out || !in) return fail(ODWF_EINVAL, "apply_normal_prec: null field");
+    if (prec == ODWF_FF) return apply_ff_normal(out, in, st);
     if (prec != ODWF_F32 && prec != ODWF_F16 && prec != ODWF_BF16)
-        return fail(ODWF_EINVAL, "apply_normal_prec: prec must be F32, F16 or BF16");
+        return fail(ODWF_EINVAL, "apply_normal_prec: prec must be F32, F16, BF16 or FF");
     if (recon != 12 && recon != 18) return fail(ODWF_EINVAL, "apply_normal_prec: link_recon must be 12 or 18");
     const Sp low = (Sp)prec;
     const size_t eb = ext_bytes(ODWF_MODE_SCHUR_EVEN);
@@ -520,6 +593,8 @@ int check_params(const odwf_solve_params* prm) {
         return fail(ODWF_EINVAL, "solve: link_recon must be 0, 12 or 18");
     if (prm->link_prec != 0 && prm->link_prec != ODWF_F32 && prm->link_prec != ODWF_F16)
         return fail(ODWF_EINVAL, "solve: link_prec must be 0, ODWF_F32 or ODWF_F16");
+    if (prm->update_arith < ODWF_UPDATES_AUTO || prm->update_arith > ODWF_UPDATES_FF)
+        return fail(ODWF_EINVAL, "solve: update_arith must be ODWF_UPDATES_AUTO, _F64 or _FF");
     if (prm->link_prec == ODWF_F16 && prm->link_recon == 18)
         return fail(ODWF_EINVAL, "solve: FP16 links are stored with 12 reals (link_recon 0 or 12)");
     return ODWF_OK;

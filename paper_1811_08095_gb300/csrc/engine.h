@@ -58,6 +58,7 @@ struct Engine {
     std::vector<double> omega;
     Coef5<double> cf64{};
     Coef5<float> cf32{};
+    Coef5<ff> cfff{};  // the FP64 coefficients as float-float pairs (reliable updates)
     int device = 0;
 
     // packed links
@@ -65,14 +66,17 @@ struct Engine {
     void* links_f18 = nullptr;
     void* links_f12 = nullptr;
     void* links_h12 = nullptr;
+    void* links_ff18 = nullptr;  // the FP64 links as float-float pairs (reliable updates)
     void* links_site[4] = {nullptr, nullptr, nullptr, nullptr};  // site-major copies by Lk (second-generation hops)
     bool have_site[4] = {false, false, false, false};
     int* nbr = nullptr;  // neighbour table of the second-generation hops (launch_build_neighbours)
     unsigned* bounds_flag = nullptr;  // device word for the debug build's index checks
     bool gauge_set = false;
     bool have_f12 = false, have_f18 = false, have_h12 = false;  // low-precision copies of the FP64 links
+    bool have_ff18 = false;
     const void* links_of(Lk lk) const {
-        return lk == Lk::F12 ? links_f12 : lk == Lk::F18 ? links_f18 : lk == Lk::H12 ? links_h12 : links_d18;
+        return lk == Lk::F12 ? links_f12 : lk == Lk::F18 ? links_f18 : lk == Lk::H12 ? links_h12
+             : lk == Lk::FF18 ? links_ff18 : links_d18;
     }
 
     // named workspaces (grow-only)
@@ -111,6 +115,7 @@ struct Engine {
     int apply(void* out, const void* in, int mode, bool dag, cudaStream_t st);
     int apply_normal(void* out, const void* in, int system, cudaStream_t st);
     int apply_m5(void* out, const void* in, long n_sites, int op, cudaStream_t st);
+    int apply_ff_normal(void* out, const void* in, cudaStream_t st);
     int apply_low_normal(void* out, const void* in, int prec, int recon, cudaStream_t st);
     int mixed_cg_step(int prec, int recon, int link_prec, double mq_step, const void* p_prev, const void* r, const void* x,
                       void* const* outs, odwf_cg_step_scalars* sc, cudaStream_t st);

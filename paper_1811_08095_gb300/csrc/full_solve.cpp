@@ -80,7 +80,10 @@ int Engine::solve_full(void* x, const void* b, const odwf_solve_params* prm, odw
     ODWF_CK(launch_pack(Sp::F64, db, Bo.ref_sys(0), g, 1, ns, 0, st));
 
     BatchCG bc;
-    if ((rc = bc.init(this, 1, *prm, st))) return rc;
+    // the pipeline reads and writes the CG's solution and right-hand side with the FP64 kernels
+    odwf_solve_params prm64 = *prm;
+    prm64.update_arith = ODWF_UPDATES_F64;
+    if ((rc = bc.init(this, 1, prm64, st))) return rc;
     const int every = prm->check_every > 0 ? prm->check_every : 8;
     int iters = 0, nrel = 0, status = kDone;
     const size_t n5 = sites5();

@@ -203,6 +203,11 @@ __device__ __forceinline__ float warp_sum(float v) {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     return v;
 }
+__device__ __forceinline__ ff warp_sum(ff v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += shfl_down(v, off, 32);
+    return v;
+}
 
 // Deterministic block sum (fixed tree for a fixed blockDim); result valid in thread 0.
 // The per-thread values and the sum over a warp are taken in the kernel's arithmetic type

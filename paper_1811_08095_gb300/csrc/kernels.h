@@ -7,8 +7,8 @@
 
 namespace odwf {
 
-enum class Sp { F64 = 0, F32 = 1, F16 = 2, BF16 = 3 };
-enum class Lk { D18 = 0, F18 = 1, F12 = 2, H12 = 3 };
+enum class Sp { F64 = 0, F32 = 1, F16 = 2, BF16 = 3, FF = 4 };  // FF: float-float pairs (ff.cuh)
+enum class Lk { D18 = 0, F18 = 1, F12 = 2, H12 = 3, FF18 = 4 };
 
 struct FieldRef;
 template <class R>
@@ -37,6 +37,14 @@ enum class Epi {
 
 // FP64 path (double spinors, 18-real double links, FP64 arithmetic)
 cudaError_t launch_hop_f64(const HopParams<double>& P, Epi e, int nsys, cudaStream_t st);
+// Float-float path (float-float fields and links, float-float arithmetic on the FP32 pipe): the
+// reliable updates of the mixed-precision CG.  Epilogues MINV, SCHUR_MDINV, D_MINVDAG, D_NORMAL,
+// D_NORMAL_RESID.
+cudaError_t launch_hop_ff(const HopParams<ff>& P, Epi e, int nsys, cudaStream_t st);
+cudaError_t launch_m5_ff(const FieldRef& in, const FieldRef& out, size_t n_sites, int ns, const double* r_sys,
+                         int sys_base, int nsys, int op, const Coef5<ff>& cf, cudaStream_t st);
+// the FP64 links split into float-float pairs (same 144-byte records)
+cudaError_t launch_links_ff18_from_d18(const void* d18, void* ff18, size_t n_links, cudaStream_t st);
 // Mixed path (low-precision operator fields, FP32 accumulators r/x, float links, FP32 arithmetic)
 cudaError_t launch_hop_mixed(const HopParams<float>& P, Epi e, Sp low, Lk lk, int nsys, cudaStream_t st);
 

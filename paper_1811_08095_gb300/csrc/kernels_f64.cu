@@ -71,6 +71,7 @@ cudaError_t launch_pack(Sp sp, const double2* ext, const FieldRef& out, const Ge
         case Sp::F32: note_launch(); pack_kernel<SpF32><<<grid, kBS, 0, st>>>(ext, out, g, p, ns, lg, ext_mode); break;
         case Sp::F16: note_launch(); pack_kernel<SpF16><<<grid, kBS, 0, st>>>(ext, out, g, p, ns, lg, ext_mode); break;
         case Sp::BF16: note_launch(); pack_kernel<SpBF16><<<grid, kBS, 0, st>>>(ext, out, g, p, ns, lg, ext_mode); break;
+        case Sp::FF: note_launch(); pack_kernel<SpFF><<<grid, kBS, 0, st>>>(ext, out, g, p, ns, lg, ext_mode); break;
     }
     return cudaGetLastError();
 }
@@ -84,6 +85,7 @@ cudaError_t launch_unpack(Sp sp, const FieldRef& in, double2* ext, const Geom& g
         case Sp::F32: note_launch(); unpack_kernel<SpF32><<<grid, kBS, 0, st>>>(in, ext, g, p, ns, lg, ext_mode); break;
         case Sp::F16: note_launch(); unpack_kernel<SpF16><<<grid, kBS, 0, st>>>(in, ext, g, p, ns, lg, ext_mode); break;
         case Sp::BF16: note_launch(); unpack_kernel<SpBF16><<<grid, kBS, 0, st>>>(in, ext, g, p, ns, lg, ext_mode); break;
+        case Sp::FF: note_launch(); unpack_kernel<SpFF><<<grid, kBS, 0, st>>>(in, ext, g, p, ns, lg, ext_mode); break;
     }
     return cudaGetLastError();
 }
@@ -107,11 +109,14 @@ template <class SX>
 cudaError_t vec_y(Sp spy, const FieldRef& x, const FieldRef& y, size_t n5, int ns, int kind, double coef,
                   SysState* st, int gate, int need, double* partials, unsigned* counters, int sys_base,
                   int nsys, cudaStream_t stream) {
-    const bool dx = std::is_same<SX, SpF64>::value;
+    const bool dx = std::is_same<SX, SpF64>::value || std::is_same<SX, SpFF>::value;
     switch (spy) {
         case Sp::F64:
             return vec_t<SX, SpF64, double>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base,
                                             nsys, stream);
+        case Sp::FF:  // float-float storage, FP64 arithmetic (vector work is a few operations per value)
+            return vec_t<SX, SpFF, double>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base,
+                                           nsys, stream);
         case Sp::F32:
             if (dx) return vec_t<SX, SpF32, double>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
             return vec_t<SX, SpF32, float>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base,
@@ -137,6 +142,7 @@ cudaError_t launch_vec(Sp spx, Sp spy, const FieldRef& x, const FieldRef& y, siz
         case Sp::F32: return vec_y<SpF32>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
         case Sp::F16: return vec_y<SpF16>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
         case Sp::BF16: return vec_y<SpBF16>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
+        case Sp::FF: return vec_y<SpFF>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
     }
     return cudaErrorInvalidValue;
 }

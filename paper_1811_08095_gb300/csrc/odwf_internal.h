@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ff.cuh"
+
 namespace odwf {
 
 constexpr int kMaxNs = 32;
@@ -171,6 +173,31 @@ struct SpinorIO<SpF16, R> : HalfIO<__half2, R> {};
 template <class R>
 struct SpinorIO<SpBF16, R> : HalfIO<__nv_bfloat162, R> {};
 
+// Float-float storage (reliable updates of the mixed-precision CG): each real as an FP32 pair
+// (hi, lo), 192 bytes per 5D site in the FP64 chunk layout (a 16-byte chunk holds two values).
+struct SpFF { using T = float; static constexpr int NCH = 12; static constexpr bool kNorm = false; };
+
+template <class R>
+struct SpinorIO<SpFF, R> {
+    static __device__ __forceinline__ void load(const void* base, const float*, size_t h, int s, int ns, R v[24]) {
+        const float4* p = reinterpret_cast<const float4*>(base);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const float4 q = __ldg(p + chunk_off(h, k, 12, ns, s));
+            v[2 * k] = ff_to<R>(ff(q.x, q.y));
+            v[2 * k + 1] = ff_to<R>(ff(q.z, q.w));
+        }
+    }
+    static __device__ __forceinline__ void store(void* base, float*, size_t h, int s, int ns, const R v[24]) {
+        float4* p = reinterpret_cast<float4*>(base);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const ff a = to_ff(v[2 * k]), b = to_ff(v[2 * k + 1]);
+            p[chunk_off(h, k, 12, ns, s)] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        }
+    }
+};
+
 // Link field: for each parity p, direction mu and half-site h, U_mu(x) of site (p, h),
 // row-major 3x3 complex.  LinkD18: 18 doubles; LinkF18: 18 floats padded to 20;
 // LinkF12: rows 0 and 1 as 12 floats, row 2 = conj(row0 x row1) rebuilt in registers;
@@ -181,9 +208,23 @@ struct LinkD18 { static constexpr int BYTES = 144; };
 struct LinkF18 { static constexpr int BYTES = 80; };
 struct LinkF12 { static constexpr int BYTES = 48; };
 struct LinkH12 { static constexpr int BYTES = 24; };
+struct LinkFF18 { static constexpr int BYTES = 144; };  // 18 float-float pairs (the FP64 links split)
 
 template <class LK, class R>
 struct LinkIO;
+
+template <class R>
+struct LinkIO<LinkFF18, R> {
+    static __device__ __forceinline__ void load(const void* base, size_t idx, R u[18]) {
+        const float4* p = reinterpret_cast<const float4*>(reinterpret_cast<const char*>(base) + idx * 144);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float4 q = __ldg(p + k);
+            u[2 * k] = ff_to<R>(ff(q.x, q.y));
+            u[2 * k + 1] = ff_to<R>(ff(q.z, q.w));
+        }
+    }
+};
 
 template <class R>
 struct LinkIO<LinkD18, R> {
@@ -296,6 +337,18 @@ template <class R>
 __device__ __forceinline__ R shfl_up(R v, int d, int width) { return __shfl_up_sync(0xffffffffu, v, d, width); }
 template <class R>
 __device__ __forceinline__ R shfl_down(R v, int d, int width) { return __shfl_down_sync(0xffffffffu, v, d, width); }
+template <>
+__device__ __forceinline__ ff shfl_idx<ff>(ff v, int src, int width) {
+    return ff(__shfl_sync(0xffffffffu, v.hi, src, width), __shfl_sync(0xffffffffu, v.lo, src, width));
+}
+template <>
+__device__ __forceinline__ ff shfl_up<ff>(ff v, int d, int width) {
+    return ff(__shfl_up_sync(0xffffffffu, v.hi, d, width), __shfl_up_sync(0xffffffffu, v.lo, d, width));
+}
+template <>
+__device__ __forceinline__ ff shfl_down<ff>(ff v, int d, int width) {
+    return ff(__shfl_down_sync(0xffffffffu, v.hi, d, width), __shfl_down_sync(0xffffffffu, v.lo, d, width));
+}
 
 // Bidiagonal fifth-dimension operator on the lane group (cyclic, corner -r):
 //   dag = false:  (X v)_s = a_s v_s + b_s (L v)_s          (X = B with a=rho, b=sigma; X = M with a=d, b=e)

@@ -154,8 +154,9 @@ size_t per_system_bytes(size_t sites5, int prec) {
 }
 
 size_t group_fixed_bytes(size_t vh, size_t sites5) {
-    // links (FP64, FP32-18, FP32-12 and its site-major copy), FP64 temporaries, scratch
-    return 8 * vh * (144 + 80 + 48 + 96) + sites5 * 192 * 6 + (1 << 20);
+    // links (FP64, float-float, FP32-18, FP32-12 and its site-major copy), FP64 / float-float
+    // temporaries, scratch
+    return 8 * vh * (144 + 144 + 80 + 48 + 96) + sites5 * 192 * 6 + (1 << 20);
 }
 
 std::string group_key(const odwf_request& r, const std::vector<double>& om) {
