@@ -601,6 +601,32 @@ def run_flow(args, world, rank, local):
                "sample": "one oracle Runge-Kutta step on an 8^4 field of the same recipe (%.2f s, numpy in one "
                          "thread), scaled by the site count to %s" % (sec, "x".join(map(str, dims)))}
 
+    full = None
+    if args.flow_to > 0:
+        # the paper's protocol (Sec. 2-3): flow from t = 0 to t_end in steps of 0.01, E(t) for
+        # t0, then the admissibility bound and the clover charge
+        Uf = syn.gauge_field_torch(dims, args.flow_to_eps, 4, device=dev)
+        f2 = odwf.Flow(dims)
+        f2.set_gauge(Uf, stream=stream)
+        del Uf
+        nsteps = int(round(args.flow_to / FLOW_EPS))
+        torch.cuda.synchronize()
+        t_f = time.perf_counter()
+        rec = f2.run(FLOW_EPS, nsteps, measure_every=10, stream=stream)
+        wall = time.perf_counter() - t_f
+        f2.close()
+        adm = next((o["t"] for o in rec if o["plaq_min"] > 44.0 / 45.0), None)
+        t0 = odwf.odwf_flow_t0(rec, 0.3)
+        qs = [o["q_clover"] for o in rec]
+        full = {"field": "U = exp(%g i H), H Gaussian traceless Hermitian (seed 4)" % args.flow_to_eps,
+                "t_end": round(nsteps * FLOW_EPS, 4), "steps": nsteps, "measurements": len(rec),
+                "wall_s": round(wall, 2), "t0_from_t2E_0.3": t0,
+                "t2E_max": round(max(o["t"] ** 2 * o["e_clover"] for o in rec), 6),
+                "first_admissible_t": adm, "q_clover_end": round(qs[-1], 6),
+                "q_clover_at": {str(round(o["t"], 2)): round(o["q_clover"], 5)
+                                for o in rec if round(o["t"], 2) in (0.0, 1.0, 4.0, 16.0, 32.0, 48.0, 64.0)},
+                "plaq_min_end": round(rec[-1]["plaq_min"], 8), "e_clover_end": rec[-1]["e_clover"]}
+
     seg = sum(seg_ms) / len(seg_ms)
     value = world * FLOW_SEGMENT / (seg / 1e3)
     if rank == 0:
@@ -620,7 +646,7 @@ def run_flow(args, world, rank, local):
                        "observables": [{k: (round(v, 8) if isinstance(v, float) else v) for k, v in o.items()}
                                        for o in (obs[0], obs[-1])]},
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk,
+            "clocks": clk, "flow_protocol": full,
         }
         print(json.dumps(line), flush=True)
 
@@ -997,6 +1023,12 @@ def main():
     ap.add_argument("--ns", type=int, default=NS, help="profile: Ns")
     ap.add_argument("--nsys", type=int, default=3, help="profile: systems")
     ap.add_argument("--flow-dims", type=int, nargs=4, default=list(FLOW_DIMS), help="flow: lattice")
+    ap.add_argument("--flow-to", type=float, default=0.0,
+                    help="flow: also integrate a fresh field from t = 0 to this flow time (the paper: 64), "
+                         "measuring every 10 steps, and report t0, the admissibility time and Q")
+    ap.add_argument("--flow-to-eps", type=float, default=1.0,
+                    help="flow --flow-to: strength of the random field it flows (1.0: disordered enough that "
+                         "t^2 E reaches 0.3 and the field carries topology)")
     ap.add_argument("--iters", type=int, default=4, help="profile: CG iterations")
     ap.add_argument("--rate", type=float, default=50.0, help="serve: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
