@@ -39,9 +39,10 @@ def _gpu_flow(torch, U, eps, nsteps, every):
     return out.cpu().numpy(), obs
 
 
-@pytest.mark.parametrize("dims", [(6, 4, 8, 5), (5, 3, 4, 6), (4, 6, 4, 8)])
+@pytest.mark.parametrize("dims", [(6, 4, 8, 5), (5, 3, 4, 6), (4, 6, 4, 8), (2, 2, 2, 2)])
 def test_flow_matches_oracle(dims):
-    """Ten steps on small lattices (ragged last block, odd extents, time slabs of 1, 2 and 8)."""
+    """Ten steps on small lattices (ragged last block, odd extents, time slabs of 1, 2 and 8, and
+    the minimal 2^4 lattice, where x + mu and x - mu are the same site)."""
     torch = torch_cuda()
     U = syn.gauge_field(dims, 0.6, 101)
     eps, n, every = 0.02, 10, 5
