@@ -371,6 +371,22 @@ __device__ __forceinline__ void block_sum_min(double a, float m, double* out_a, 
 
 // A_{mu nu}(x) = ta(P_{mu nu}(x)) for the six planes, one thread per site.  With MEASURE,
 // per-block sum and minimum of Re tr P over the block's plaquettes.
+// rows 0 and 1 of a b (a given by its first two rows), row 2 rebuilt: a b is in SU(3)
+__device__ __forceinline__ M3 mul_rows01(const M3& a, const M3& b) {
+    M3 c;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            c.m[3 * i + j] = cfma(a.m[3 * i + 2], b.m[6 + j], cfma(a.m[3 * i + 1], b.m[3 + j], cmul(a.m[3 * i], b.m[j])));
+    third_row(c);
+    return c;
+}
+
+// A_{mu nu}(x) = ta(P_{mu nu}(x)) for the six planes, one thread per site.  The site's own four
+// links are read once and kept as their first two rows (they are only ever left factors); the
+// two products of each plaquette are formed as two rows with the third rebuilt (they are SU(3)).
+// With MEASURE, per-block sum and minimum of Re tr P over the block's plaquettes.
 template <bool MEASURE>
 __global__ void __launch_bounds__(kBS) plaq_kernel(FlowGeom g, const float4* __restrict__ hi, float4* __restrict__ A,
                                                    double* __restrict__ part_retr, float* __restrict__ part_min) {
@@ -379,15 +395,17 @@ __global__ void __launch_bounds__(kBS) plaq_kernel(FlowGeom g, const float4* __r
     double rsum = 0.0;
     float rmin = 3.0f;
     if (ok) {
+        M3 own[4];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) load_rows(hi, g.V, mu, st.s, own[mu]);
 #pragma unroll
         for (int mu = 0; mu < 3; ++mu) {
-            const M3 um = load_link(hi, g.V, mu, st.s);
             const size_t xm = step(g, st, mu, +1);
 #pragma unroll
             for (int nu = mu + 1; nu < 4; ++nu) {
                 const size_t xn = step(g, st, nu, +1);
-                const M3 t1 = mul(um, load_link(hi, g.V, nu, xm));                             // U_mu(x) U_nu(x+mu)
-                const M3 t2 = mul(load_link(hi, g.V, nu, st.s), load_link(hi, g.V, mu, xn));  // U_nu(x) U_mu(x+nu)
+                const M3 t1 = mul_rows01(own[mu], load_link(hi, g.V, nu, xm));  // U_mu(x) U_nu(x+mu)
+                const M3 t2 = mul_rows01(own[nu], load_link(hi, g.V, mu, xn));  // U_nu(x) U_mu(x+nu)
                 float retr;
                 store_ah(A, g.V, plane_of(mu, nu), st.s, ta_mul_dag(t1, t2, &retr));
                 if (MEASURE) {
