@@ -259,28 +259,39 @@ __device__ __forceinline__ void finalize_scalar(SysState* st, double total, int 
 
 // Block-level reduction of `v` for system `sys`; the last block to arrive sums the
 // partials in index order and finalizes.
+// Per-block sum of v (the kernel's arithmetic type within a warp, FP64 across warps), written to
+// the system's partial of this block; the last block to finish (counted atomically) sums the
+// partials in index order and finalizes the scalar.  One block barrier: after it the other warps
+// leave and warp 0 alone writes the partial and, in the last block, sums all partials.  The sum
+// order is fixed whatever block finishes last, so results are deterministic.  Must be the
+// kernel's last statement (warps other than 0 return here).
 template <class R>
 __device__ __forceinline__ void reduce_and_finalize(R v, double* partials, unsigned* counters, SysState* st,
                                                     int sys, int fin) {
     __shared__ double sm[32];
-    __shared__ bool is_last;
-    const double bs = block_sum(v, sm);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    if (lane == 0) sm[wid] = (double)v;
+    __syncthreads();
+    if (wid != 0) return;
+    double bs = lane < nw ? sm[lane] : 0.0;
+    bs = warp_sum(bs);
     const int nb = gridDim.x;
     double* part = partials + (size_t)sys * nb;
-    if (threadIdx.x == 0) {
+    unsigned prev = 0;
+    if (lane == 0) {
         part[blockIdx.x] = bs;
         __threadfence();
-        const unsigned prev = atomicAdd(counters + sys, 1u);
-        is_last = (prev == (unsigned)(nb - 1));
+        prev = atomicAdd(counters + sys, 1u);
     }
-    __syncthreads();
-    if (!is_last) return;
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev != (unsigned)(nb - 1)) return;
     __threadfence();
     double t = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) t += *((volatile double*)(part + i));
-    const double total = block_sum<double>(t, sm);
-    if (threadIdx.x == 0) {
-        finalize_scalar(st + sys, total, fin);
+    for (int i = lane; i < nb; i += 32) t += *((volatile double*)(part + i));
+    t = warp_sum(t);
+    if (lane == 0) {
+        finalize_scalar(st + sys, t, fin);
         counters[sys] = 0u;
     }
 }
