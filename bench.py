@@ -948,28 +948,68 @@ def run_residual_mass(args, world, rank, local):
     """Residual mass and pseudoscalar correlator of the effective 4D operator (Sec. 3, Table 1's
     quantity) on a synthetic field: 16^4 x 16 (links exp(0.25 i H), seed 13), point source at
     the origin, twelve effective solves per mass (FULL_DIRAC through the mixed-precision Schur
-    CG, tolerance 1e-10).  Reports m_res per mass, the solve time and iteration counts."""
+    CG, tolerance 1e-10).  Reports m_res per mass, the solve time and iteration counts, the
+    dominant kernel's roofline from the library's per-launch events, and the oracle's time for the
+    same inner iterations (one oracle S^dag S CG iteration on this field, timed on the host cores,
+    times the GPU's iteration count)."""
     import torch
 
     import odwf_synth as syn
+    import oracle
     import paper_1811_08095_gb300 as odwf
 
     torch.cuda.set_device(local)
+    lib = odwf.load()
     dims = tuple(args.dims) if args.dims != list(DIMS) else (16, 16, 16, 16)
     w, _ = odwf.odwf_zolotarev_omega(args.ns, LRANGE[0], LRANGE[1])
     h = odwf.Handle(dims, args.ns, M0, 0.04, w)
-    h.set_gauge(syn.gauge_field_torch(dims, EPS, 13, device="cuda"))
+    Ud = syn.gauge_field_torch(dims, EPS, 13, device="cuda")
+    h.set_gauge(Ud)
     out = []
+    lib.odwf_profile_enable(1)
+    gpu_s = 0.0
+    iters_total = 0
     for mq in (0.04, 0.5):
         t = time.perf_counter()
         mres, corr, st = h.residual_mass((0, 0, 0, 0), tol=TOL, prec=args.prec, mq=mq)
-        out.append({"mq": mq, "m_res": mres, "m_res_over_mq": mres / mq, "seconds": round(time.perf_counter() - t, 2),
+        dt = time.perf_counter() - t
+        gpu_s += dt
+        iters_total += st["iters"]
+        out.append({"mq": mq, "m_res": mres, "m_res_over_mq": mres / mq, "seconds": round(dt, 2),
                     "inner_iters_12_solves": st["iters"], "worst_true_resid": st["true_resid"],
                     "corr_t0_t1_tmid": [corr[0], corr[1], corr[len(corr) // 2]]})
+    torch.cuda.synchronize()
+    prof = read_profile(lib)
+    lib.odwf_profile_enable(0)
     h.close()
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if prof:
+        dom = max(prof, key=lambda e: e["total_ms"])
+        per_launch = (dom["system_launches"] * dom["bytes_per_system"] + dom["launches"] * dom["bytes_per_launch"]) \
+            / dom["launches"]
+        achieved = per_launch / (dom["total_ms"] / dom["launches"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "share_of_gpu_time": round(dom["total_ms"] / sum(
+                    e["total_ms"] for e in prof), 4), "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)",
+                "timing": "the library's per-launch CUDA events during the 24 solves"}
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        U = Ud.cpu().numpy()
+        b = syn.gaussian_spinor_even(args.ns, dims, 5)
+        t = time.perf_counter()
+        oracle.cg(U, b, M0, 0.04, w, tol=1e-30, max_iter=1)
+        spi = (time.perf_counter() - t) / 3.0  # initial residual, one iteration, final residual
+        cpu = {"seconds_for_the_same_inner_iterations": round(spi * iters_total, 1), "cores": oracle.num_threads(),
+               "kind": "oracle", "gpu_seconds": round(gpu_s, 2), "ratio": round(spi * iters_total / gpu_s, 1),
+               "sample": "one FP64 oracle S^dag S CG iteration on this 16^4 x 16 field (%.2f s on %d threads), "
+                         "times the %d inner iterations of the GPU's 24 solves (the FP64 reconstruction and "
+                         "refinement steps not counted)" % (spi, oracle.num_threads(), iters_total)}
+    del Ud
     print(json.dumps({"workload": "residual_mass_%s_ns%d" % ("x".join(map(str, dims)), args.ns),
                       "metric": "residual mass of the effective operator (point source, 12 solves per mass)",
                       "prec": args.prec, "omega": "shifted (R5) Zolotarev on [0.05, 6.2]", "results": out,
+                      "roofline": roof, "cpu_baseline": cpu,
                       "reading": "m_res = tr G_00 / sum_x tr(G_x0^dag G_x0) - m_q, G = (D_eff^-1 - 1)/(2 m0 - m_q)"}),
           flush=True)
 

@@ -67,7 +67,9 @@ int odwf_flow_create(const int32_t dims[4], odwf_flow** out);
 int odwf_flow_destroy(odwf_flow* f);
 
 /* Load the gauge field U (host or device, complex128, V * 36 entries) as the flow's field at t = 0.
- * U must be in SU(3): the third row of each link is not read but rebuilt from the first two. */
+ * U must be in SU(3): the third row of each link is not read but rebuilt from the first two.  With
+ * a host U the copy goes through a device staging buffer of one direction (V * 144 bytes) that the
+ * object keeps until odwf_flow_destroy; the call returns once U may be reused. */
 int odwf_flow_set_gauge(odwf_flow* f, const void* U, void* stream);
 
 /* Write the current (flowed) field to U (host or device, complex128, layout above). */

@@ -29,6 +29,7 @@ struct odwf_flow {
     double* part_q = nullptr;
     FlowObsDev* obs_dev = nullptr;
     int obs_cap = 0;
+    double2* stage = nullptr;  // host-pointer gauge copies: one direction at a time, kept until destroy
     bool gauge_set = false;
 };
 
@@ -73,6 +74,7 @@ void release(odwf_flow* f) {
     cudaFree(f->part_e);
     cudaFree(f->part_q);
     cudaFree(f->obs_dev);
+    cudaFree(f->stage);
 }
 
 int on_device(const odwf_flow* f, const char* fn) {
@@ -217,11 +219,11 @@ int odwf_flow_set_gauge(odwf_flow* f, const void* U, void* stream) {
     const size_t V = f->g.V;
     const size_t slab = 9 * V * sizeof(double2);  // one direction
     const bool dev = odwf::is_device_ptr(U);
-    double2* stage = nullptr;
-    if (!dev) {
-        rc = alloc((void**)&stage, slab, "gauge staging");
+    if (!dev && !f->stage) {
+        rc = alloc((void**)&f->stage, slab, "gauge staging");
         if (rc) return rc;
     }
+    double2* stage = dev ? nullptr : f->stage;
     for (int mu = 0; mu < 4 && !rc; ++mu) {
         const double2* src = (const double2*)U + (size_t)mu * 9 * V;
         if (!dev) {
@@ -235,10 +237,9 @@ int odwf_flow_set_gauge(odwf_flow* f, const void* U, void* stream) {
             if (e != cudaSuccess) rc = cuda_fail(e, "flow split kernel");
         }
     }
-    if (stage) {
+    if (stage) {  // the caller may reuse its host buffer on return
         const cudaError_t e = cudaStreamSynchronize(st);
         if (!rc && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
-        cudaFree(stage);
     }
     if (!rc) f->gauge_set = true;
     return rc;
@@ -257,11 +258,11 @@ int odwf_flow_get_gauge(odwf_flow* f, void* U, void* stream) {
     const size_t V = f->g.V;
     const size_t slab = 9 * V * sizeof(double2);
     const bool dev = odwf::is_device_ptr(U);
-    double2* stage = nullptr;
-    if (!dev) {
-        rc = alloc((void**)&stage, slab, "gauge staging");
+    if (!dev && !f->stage) {
+        rc = alloc((void**)&f->stage, slab, "gauge staging");
         if (rc) return rc;
     }
+    double2* stage = dev ? nullptr : f->stage;
     for (int mu = 0; mu < 4 && !rc; ++mu) {
         double2* dst = dev ? (double2*)U + (size_t)mu * 9 * V : stage;
         cudaError_t e = odwf::flow::launch_join(f->hi[f->cur], f->lo[f->cur], dst, V, mu, st);
@@ -273,7 +274,6 @@ int odwf_flow_get_gauge(odwf_flow* f, void* U, void* stream) {
             if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync (gauge)");
         }
     }
-    if (stage) cudaFree(stage);
     return rc;
     FGUARD_END
 }
