@@ -33,7 +33,7 @@ import numpy as np
 __all__ = [
     "gell_mann", "gauge_field", "gauge_field_torch", "gaussian_spinor",
     "gaussian_spinor_even", "point_source", "random_site", "random_even_site", "volume",
-    "even_sites", "flux_field", "abelian_wave_field",
+    "even_sites", "flux_field", "abelian_wave_field", "gaussian_momenta",
 ]
 
 
@@ -195,3 +195,12 @@ def abelian_wave_field(dims, mu: int, nu: int, amp: float, n: int, charges=(1, -
     phi = np.zeros((4, lt, lz, ly, lx))
     phi[mu] = amp * np.cos(2.0 * np.pi * n * X[nu] / L[nu])
     return _abelian_links(phi, charges)
+
+
+def gaussian_momenta(dims, seed: int) -> np.ndarray:
+    """Molecular-dynamics momenta P = sum_a p_a T_a with T_a = i lambda_a / 2 and p_a ~ N(0, 1)
+    (traceless anti-Hermitian), shape (4, Lt, Lz, Ly, Lx, 3, 3) like the gauge field."""
+    lx, ly, lz, lt = dims
+    rng = np.random.default_rng(seed)
+    p = rng.standard_normal((4, lt, lz, ly, lx, 8))
+    return np.einsum("...a,aij->...ij", p, 1j * gell_mann() / 2)

@@ -7,7 +7,9 @@ links or calls anything here, and this package imports nothing from it.
 `odwf_oracle.c` holds the operator (naive loops, definitions written out, see its
 header); `zolotarev.py` the optimal weights; `dense.py` dense-matrix builds for the
 identities of Sec. 2; `flow.py` the gradient flow of the gauge field and the flow
-observables (energy density, clover charge, admissibility) of Sec. 2-3.  Parity status: every function here is pinned by tests under
+observables (energy density, clover charge, admissibility) of Sec. 2-3; `hmc.py` the
+two-flavour pseudofermion action and force, the Wilson gauge force and the molecular-dynamics
+integrators of the paper's HMC (Sec. 2).  Parity status: every function here is pinned by tests under
 `tests/test_oracle_*.py` (free-field closed form, gamma_5-hermiticity, gauge
 covariance, dense adjoint, the effective-operator / shifted-Zolotarev identity of
 Sec. 2, the determinant-ratio identity of Eq. (1)-(2), dense Schur complement, dense
