@@ -349,6 +349,24 @@ int odwf_profile_enable(int on);
 int odwf_profile_read(odwf_kernel_prof* out, int max_entries, int* n_out);
 
 /*
+ * Two-flavour pseudofermion action and its force (Sec. 2: the two-flavour parts of the HMC, with
+ * mass preconditioning by auxiliary heavy masses).  The action's formula is cited by the paper,
+ * not printed; this is the ratio form: det D(m) = det(M(m))^2 det S(m) with M free of links, so
+ *     S_pf = phi^+ S(m2)^+ (S(m1)^+ S(m1))^-1 S(m2) phi = |S(m1) X|^2,  X = (S(m1)^+ S(m1))^-1 S(m2) phi
+ * represents det[D(m1)^+ D(m1)] / det[D(m2)^+ D(m2)]: m2 = 2 m0 (Pauli-Villars) is the plain
+ * two-flavour factor, a chain m_q -> m_H1 -> m_H2 -> 2 m0 the mass-preconditioned product.
+ * phi: even-site field (host or device, SCHUR_EVEN layout).  The solve for X runs with `params`
+ * (tol, max_iter, prec, delta, ...; system and mq are set here) and its statistics go to stats
+ * (may be NULL).  action (host): S_pf.  force (host or device, complex128, gauge layout
+ * [mu][t][z][y][x][3][3], or NULL): per link the traceless anti-Hermitian Pi with
+ * dS_pf/deps = tr(T Pi) for U_mu(x) -> exp(eps T) U_mu(x), T traceless anti-Hermitian.
+ * Everything but the inner solve is FP64.  Allocates its FP64 workspaces on the handle (nine
+ * even-site fields and the per-link sums).  Synchronises `stream`.
+ */
+int odwf_pf_force(odwf_handle* h, const void* phi, double m1, double m2, const odwf_solve_params* params,
+                  double* action, void* force, odwf_solve_stats* stats, void* stream);
+
+/*
  * Time one kernel of the production mixed-precision iteration on its own: kind 1..4 = the
  * hops K1..K4 (see odwf_mixed_cg_step; K1 is the plain Dslash chi_t = B M^-1 (-1/2 W chi_p)),
  * 5 = the p update.  nsys systems (1..64) share the handle's links; every input field of every

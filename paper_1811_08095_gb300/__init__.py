@@ -257,6 +257,18 @@ class Handle:
         d["rc"] = rc
         return d
 
+    def pf_force(self, phi, m1, m2, force=None, tol=1e-10, max_iter=100000, prec="f64", updates="auto",
+                 stream=None):
+        """odwf_pf_force: the two-flavour pseudofermion action phi^+ S2^+ (S1^+ S1)^-1 S2 phi and,
+        when `force` (a complex128 buffer of the gauge field's shape) is given, its force.
+        Returns (action, stats dict)."""
+        p = _params(tol, max_iter, prec, 0.01, ODWF_SYS_SCHUR_NORMAL, 12, None, 8, "f32", updates)
+        st = _lib.odwf_solve_stats()
+        act = ctypes.c_double(0.0)
+        check(self._lib.odwf_pf_force(self._h, ptr(phi), float(m1), float(m2), ctypes.byref(p), ctypes.byref(act),
+                                      ptr(force), ctypes.byref(st), stream_ptr(stream)))
+        return act.value, _stats_dict(st)
+
     def residual_mass(self, site, tol=1e-10, max_iter=100000, prec="f64", mq=None, stream=None):
         """odwf_residual_mass at site (x, y, z, t): returns (m_res, C(t) array, stats dict)."""
         p = _params(tol, max_iter, prec, 0.01, ODWF_SYS_FULL_DIRAC, 12, mq, 8)

@@ -116,6 +116,7 @@ _SIGS = {
     "serve_destroy": ([P], I),
     "serve_set_policy": ([P, D, I, I], I),
     "serve_cancel": ([P, ctypes.c_uint64], I),
+    "odwf_pf_force": ([P, P, D, D, ctypes.POINTER(odwf_solve_params), ctypes.POINTER(D), P, P, P], I),
     "odwf_flow_create": ([ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(P)], I),
     "odwf_flow_destroy": ([P], I),
     "odwf_flow_set_gauge": ([P, P, P], I),

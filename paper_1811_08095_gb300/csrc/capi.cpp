@@ -173,6 +173,15 @@ int odwf_effective_solve(odwf_handle* h, void* x, const void* b, const odwf_solv
     GUARD_END
 }
 
+int odwf_pf_force(odwf_handle* h, const void* phi, double m1, double m2, const odwf_solve_params* params,
+                  double* action, void* force, odwf_solve_stats* stats, void* stream) {
+    GUARD_BEGIN
+    if (!h) return fail(ODWF_EINVAL, "odwf_pf_force: null handle");
+    ON_DEVICE(h, "odwf_pf_force", phi, force);
+    WITH_BOUNDS(h, h->e.pf_force(phi, m1, m2, params, action, force, stats, (cudaStream_t)stream), stream);
+    GUARD_END
+}
+
 int odwf_residual_mass(odwf_handle* h, const int32_t* site, const odwf_solve_params* params, double* mres,
                        double* corr, odwf_solve_stats* stats, void* stream) {
     GUARD_BEGIN

@@ -115,6 +115,8 @@ struct Engine {
     int apply(void* out, const void* in, int mode, bool dag, cudaStream_t st);
     int apply_normal(void* out, const void* in, int system, cudaStream_t st);
     int apply_m5(void* out, const void* in, long n_sites, int op, cudaStream_t st);
+    int pf_force(const void* phi, double m1, double m2, const odwf_solve_params* prm, double* action, void* force,
+                 odwf_solve_stats* stats, cudaStream_t st);
     int apply_ff_normal(void* out, const void* in, cudaStream_t st);
     int apply_low_normal(void* out, const void* in, int prec, int recon, cudaStream_t st);
     int mixed_cg_step(int prec, int recon, int link_prec, double mq_step, const void* p_prev, const void* r, const void* x,

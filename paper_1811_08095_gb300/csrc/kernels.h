@@ -43,6 +43,16 @@ cudaError_t launch_hop_f64(const HopParams<double>& P, Epi e, int nsys, cudaStre
 cudaError_t launch_hop_ff(const HopParams<ff>& P, Epi e, int nsys, cudaStream_t st);
 cudaError_t launch_m5_ff(const FieldRef& in, const FieldRef& out, size_t n_sites, int ns, const double* r_sys,
                          int sys_base, int nsys, int op, const Coef5<ff>& cf, cudaStream_t st);
+// Pseudofermion-force contraction (kernels_force.cu): G += coef * [U K1 - K2 U^+] per link from the
+// parity-split FP64 fields L (Le, Lo) and R (Re, Ro); G in the internal link order
+// ((p * 4 + mu) * Vh + h) * 9.  finalize: ta(G) into the external gauge layout.
+cudaError_t launch_force_contract(const Geom& g, int ns, const void* links_d18, const FieldRef& Le, const FieldRef& Lo,
+                                  const FieldRef& Re, const FieldRef& Ro, double coef, double2* G, bool accumulate_into,
+                                  cudaStream_t st);
+cudaError_t launch_force_finalize(const Geom& g, const double2* G, double2* out_ext, cudaStream_t st);
+// sum of squares of n doubles into *out (deterministic two-pass; partials: sumsq_partials() doubles)
+size_t sumsq_partials();
+cudaError_t launch_sumsq(const double* a, size_t n, double* partials, double* out, cudaStream_t st);
 // the FP64 links split into float-float pairs (same 144-byte records)
 cudaError_t launch_links_ff18_from_d18(const void* d18, void* ff18, size_t n_links, cudaStream_t st);
 // Mixed path (low-precision operator fields, FP32 accumulators r/x, float links, FP32 arithmetic)
