@@ -367,6 +367,41 @@ int odwf_pf_force(odwf_handle* h, const void* phi, double m1, double m2, const o
                   double* action, void* force, odwf_solve_stats* stats, void* stream);
 
 /*
+ * Wilson plaquette gauge action and force (Sec. 2: the gauge action of the HMC at beta = 6/g0^2).
+ * U: gauge field (host or device, complex128, [mu][t][z][y][x][3][3], the layout of
+ * odwf_set_gauge; need not be the handle's field, which this call leaves unchanged).
+ * action (host): S_g = beta sum_plaquettes (1 - Re tr P / 3).  force (host or device, the layout
+ * of U, or NULL): per link Pi_mu(x) = -(beta/3) ta(U_mu(x) Sigma_mu(x)), Sigma the sum of the six
+ * staples and ta the traceless anti-Hermitian part, so that dS_g/deps = tr(T Pi) for
+ * U_mu(x) -> exp(eps T) U_mu(x).  FP64; the sum over links is in a fixed order (deterministic).
+ * Synchronises `stream`.
+ */
+int odwf_gauge_force(odwf_handle* h, const void* U, double beta, double* action, void* force, void* stream);
+
+/*
+ * One molecular-dynamics trajectory of the HMC (Sec. 2: Wilson gauge action, two-flavour
+ * pseudofermion terms with mass preconditioning, the Omelyan integrator) for
+ *     H = K(P) + S_g(U) + sum_i S_pf(U; phi_i, m1[i], m2[i]),   K = -sum_links tr(P^2),
+ * integrating dU/dt = P U, dP/dt = Pi / 2 (Pi the sum of the forces of odwf_gauge_force and
+ * odwf_pf_force) over time tau in nsteps steps of eps = tau / nsteps.
+ * integrator 0: leapfrog, P += eps/4 Pi, U <- exp(eps P) U, P += eps/4 Pi.
+ * integrator 1: Omelyan (minimum norm, second order, lambda = 0.1931833275037836),
+ *   P += lambda eps/2 Pi, U <- exp(eps/2 P) U, P += (1 - 2 lambda) eps/2 Pi, U <- exp(eps/2 P) U,
+ *   P += lambda eps/2 Pi.
+ * U, P: device memory, complex128, gauge layout; updated in place.  P traceless anti-Hermitian.
+ * phi[i] (host or device, SCHUR_EVEN layout), m1[i], m2[i] (host): 0 <= nterms <= 16 pseudofermion
+ * terms; every solve runs with `params` (system and mq set per term).  energies (host, 2): H at
+ * the start and at the end.  The handle's gauge field is replaced by U at every force
+ * evaluation and holds the final U on return.  FP64 except the inner solves.  No accept/reject
+ * step and no momentum refresh: the caller draws P and phi and decides.  Synchronises `stream`.
+ * Errors: ODWF_EINVAL for null or host U/P, nterms out of range, nsteps < 0, non-finite tau
+ * or beta, an unknown integrator or bad params; the solver's codes from the inner solves.
+ */
+int odwf_md_trajectory(odwf_handle* h, void* U, void* P, int nterms, const void* const* phi, const double* m1,
+                       const double* m2, double beta, double tau, int nsteps, int integrator,
+                       const odwf_solve_params* params, double* energies, void* stream);
+
+/*
  * Time one kernel of the production mixed-precision iteration on its own: kind 1..4 = the
  * hops K1..K4 (see odwf_mixed_cg_step; K1 is the plain Dslash chi_t = B M^-1 (-1/2 W chi_p)),
  * 5 = the p update.  nsys systems (1..64) share the handle's links; every input field of every

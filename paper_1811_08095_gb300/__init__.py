@@ -269,6 +269,30 @@ class Handle:
                                       ptr(force), ctypes.byref(st), stream_ptr(stream)))
         return act.value, _stats_dict(st)
 
+    def gauge_force(self, U, beta, force=None, stream=None):
+        """odwf_gauge_force: the Wilson plaquette action of U (host array or device tensor of the
+        gauge field's shape) and, when `force` is given, its force Pi into it.  Returns the action."""
+        act = ctypes.c_double(0.0)
+        check(self._lib.odwf_gauge_force(self._h, ptr(U), float(beta), ctypes.byref(act), ptr(force),
+                                         stream_ptr(stream)))
+        return act.value
+
+    def md_trajectory(self, U, P, terms, beta, tau, nsteps, integrator="omelyan", tol=1e-10, max_iter=100000,
+                      prec="f64", updates="auto", stream=None):
+        """odwf_md_trajectory: integrate (U, P) (device tensors, updated in place) over time tau in
+        nsteps steps; terms = [(phi, m1, m2), ...].  Returns (H_start, H_end)."""
+        n = len(terms)
+        integ = {"leapfrog": 0, "omelyan": 1}[integrator]
+        p = _params(tol, max_iter, prec, 0.01, ODWF_SYS_SCHUR_NORMAL, 12, None, 8, "f32", updates)
+        phis = (ctypes.c_void_p * max(n, 1))(*[ptr(t[0]).value for t in terms])
+        m1 = np.ascontiguousarray([t[1] for t in terms] or [0.0], dtype=np.float64)
+        m2 = np.ascontiguousarray([t[2] for t in terms] or [0.0], dtype=np.float64)
+        en = np.zeros(2, dtype=np.float64)
+        check(self._lib.odwf_md_trajectory(self._h, ptr(U), ptr(P), n, ctypes.cast(phis, ctypes.c_void_p), ptr(m1),
+                                           ptr(m2), float(beta), float(tau), int(nsteps), integ, ctypes.byref(p),
+                                           ptr(en), stream_ptr(stream)))
+        return float(en[0]), float(en[1])
+
     def residual_mass(self, site, tol=1e-10, max_iter=100000, prec="f64", mq=None, stream=None):
         """odwf_residual_mass at site (x, y, z, t): returns (m_res, C(t) array, stats dict)."""
         p = _params(tol, max_iter, prec, 0.01, ODWF_SYS_FULL_DIRAC, 12, mq, 8)

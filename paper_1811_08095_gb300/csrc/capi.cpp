@@ -182,6 +182,28 @@ int odwf_pf_force(odwf_handle* h, const void* phi, double m1, double m2, const o
     GUARD_END
 }
 
+int odwf_gauge_force(odwf_handle* h, const void* U, double beta, double* action, void* force, void* stream) {
+    GUARD_BEGIN
+    if (!h) return fail(ODWF_EINVAL, "odwf_gauge_force: null handle");
+    ON_DEVICE(h, "odwf_gauge_force", U, force);
+    WITH_BOUNDS(h, h->e.gauge_force_api(U, beta, action, force, (cudaStream_t)stream), stream);
+    GUARD_END
+}
+
+int odwf_md_trajectory(odwf_handle* h, void* U, void* P, int nterms, const void* const* phi, const double* m1,
+                       const double* m2, double beta, double tau, int nsteps, int integrator,
+                       const odwf_solve_params* params, double* energies, void* stream) {
+    GUARD_BEGIN
+    if (!h) return fail(ODWF_EINVAL, "odwf_md_trajectory: null handle");
+    ON_DEVICE(h, "odwf_md_trajectory", U, P);
+    for (int i = 0; phi && i < nterms && i < 16; ++i) ON_DEVICE(h, "odwf_md_trajectory", phi[i]);
+    WITH_BOUNDS(h,
+                h->e.md_trajectory(U, P, nterms, phi, m1, m2, beta, tau, nsteps, integrator, params, energies,
+                                   (cudaStream_t)stream),
+                stream);
+    GUARD_END
+}
+
 int odwf_residual_mass(odwf_handle* h, const int32_t* site, const odwf_solve_params* params, double* mres,
                        double* corr, odwf_solve_stats* stats, void* stream) {
     GUARD_BEGIN

@@ -115,6 +115,11 @@ struct Engine {
     int apply(void* out, const void* in, int mode, bool dag, cudaStream_t st);
     int apply_normal(void* out, const void* in, int system, cudaStream_t st);
     int apply_m5(void* out, const void* in, long n_sites, int op, cudaStream_t st);
+    int gauge_force(const double2* U, double beta, double* action, double2* F, cudaStream_t st);
+    int gauge_force_api(const void* U, double beta, double* action, void* force, cudaStream_t st);
+    int md_trajectory(void* U, void* P, int nterms, const void* const* phi, const double* m1, const double* m2,
+                      double beta, double tau, int nsteps, int integrator, const odwf_solve_params* prm,
+                      double* energies, cudaStream_t st);
     int pf_force(const void* phi, double m1, double m2, const odwf_solve_params* prm, double* action, void* force,
                  odwf_solve_stats* stats, cudaStream_t st);
     int apply_ff_normal(void* out, const void* in, cudaStream_t st);

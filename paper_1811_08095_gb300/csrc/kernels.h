@@ -53,6 +53,15 @@ cudaError_t launch_force_finalize(const Geom& g, const double2* G, double2* out_
 // sum of squares of n doubles into *out (deterministic two-pass; partials: sumsq_partials() doubles)
 size_t sumsq_partials();
 cudaError_t launch_sumsq(const double* a, size_t n, double* partials, double* out, cudaStream_t st);
+cudaError_t launch_sum_partials(const double* partials, int nb, double* out, cudaStream_t st);  // one block, fixed order
+// Wilson gauge force and action, MD updates (kernels_md.cu), FP64 on the external gauge layout.
+// gauge force: F (may be null) = -(beta/3) ta(U Sigma) per link; *retr_sum = sum_links Re tr(U Sigma)
+// (partials: gauge_force_blocks(V) doubles)
+size_t gauge_force_blocks(size_t V);
+cudaError_t launch_gauge_force(const int dims[4], const double2* U, double beta, double2* F, double* partials,
+                               double* retr_sum, cudaStream_t st);
+cudaError_t launch_link_update(size_t nlinks, double2* U, const double2* P, double a, cudaStream_t st);  // U <- exp(aP) U
+cudaError_t launch_axpy(size_t n, double2* y, const double2* x, double c, cudaStream_t st);              // y += c x
 // the FP64 links split into float-float pairs (same 144-byte records)
 cudaError_t launch_links_ff18_from_d18(const void* d18, void* ff18, size_t n_links, cudaStream_t st);
 // Mixed path (low-precision operator fields, FP32 accumulators r/x, float links, FP32 arithmetic)

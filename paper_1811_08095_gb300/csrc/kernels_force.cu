@@ -197,6 +197,12 @@ cudaError_t launch_force_finalize(const Geom& g, const double2* G, double2* out_
 
 size_t sumsq_partials() { return kSumsqBlocks; }
 
+cudaError_t launch_sum_partials(const double* partials, int nb, double* out, cudaStream_t st) {
+    note_launch();
+    sum_partials_kernel<<<1, 256, 0, st>>>(partials, nb, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sumsq(const double* a, size_t n, double* partials, double* out, cudaStream_t st) {
     note_launch();
     sumsq_kernel<<<kSumsqBlocks, 256, 0, st>>>(a, n, partials);
