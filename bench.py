@@ -651,6 +651,151 @@ def run_flow(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+HMC_DIMS = (16, 16, 16, 32)
+HMC_BETA = 6.2
+HMC_CHAIN = (0.00125, 0.01, 0.1, 2 * M0)  # m_ud -> m_H1 -> m_H2 -> m_PV (Sec. 2 mass preconditioning)
+HMC_TAU = 0.1
+HMC_NSTEPS = 2
+HMC_INNER = 4  # gauge steps per outer drift (Sexton-Weingarten)
+HMC_WORKLOAD = "hmc_md_omelyan_16x16x16x32_ns16_2f_hasenbusch3"
+FP64_ALU_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA/clk/SM x 2 flops x max SM clock
+
+
+def run_hmc(args, world, rank, local):
+    """Molecular dynamics of the two-flavour HMC (Sec. 2: Omelyan integrator with Sexton-Weingarten
+    time scales, HMC_INNER gauge steps per outer drift; Wilson gauge action at beta = 6.2; the u/d
+    factor with two levels of mass preconditioning m_ud = 0.00125 -> m_H1 = 0.01 -> m_H2 = 0.1 ->
+    m_PV = 2.6) on 16^3 x 32 x 16, the lattice of the paper's first two-flavour DWF HMC (Sec. 5).  A bench step is one trajectory segment of HMC_NSTEPS Omelyan steps
+    (tau = HMC_TAU) from the same (U, P, phi): H at the start with the forces, two force evaluations
+    per step, H at the end; every pseudofermion solve mixed precision to 1e-10.  The metric is MD
+    steps per second; the sustained rate counts 4 x 1420 flops per 5D site per inner CG iteration
+    (the four hops of S^dag S, level-1 work and the FP64 force parts not counted)."""
+    import numpy as np
+    import torch
+
+    import odwf_synth as syn
+    import paper_1811_08095_gb300 as odwf
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = odwf.load()
+    stream = torch.cuda.current_stream()
+    dims, ns = HMC_DIMS, NS
+    V = math.prod(dims)
+    w, _ = odwf.odwf_zolotarev_omega(ns, LRANGE[0], LRANGE[1])
+    h = odwf.Handle(dims, ns, M0, HMC_CHAIN[0], w)
+    U0 = syn.gauge_field_torch(dims, EPS, 21 + rank, device=dev)
+    P0 = torch.from_numpy(syn.gaussian_momenta(dims, 22 + rank)).to(dev)
+    terms = [(torch.from_numpy(syn.gaussian_spinor_even(ns, dims, 23 + k + 10 * rank)).to(dev), HMC_CHAIN[k],
+              HMC_CHAIN[k + 1]) for k in range(3)]
+    U = torch.empty_like(U0)
+    P = torch.empty_like(P0)
+
+    def traj():
+        U.copy_(U0)
+        P.copy_(P0)
+        return h.md_trajectory(U, P, terms, HMC_BETA, HMC_TAU, HMC_NSTEPS, "omelyan", n_inner=HMC_INNER, tol=TOL,
+                               prec=args.prec, stream=stream)
+
+    for _ in range(args.warmup):
+        traj()
+    torch.cuda.synchronize()
+    launches0 = lib.odwf_launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, iters, dH, res = [], [], [], []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        H0, H1, st = traj()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        iters.append(st["iters"])
+        dH.append(H1 - H0)
+        res.append(st["true_resid"])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = lib.odwf_launch_count() - launches0
+    t_local = sum(ms) / 1e3
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    value, t_max, n_all = aggregate(t_local, HMC_NSTEPS * args.steps, dist, dev)
+
+    # per-launch events over one more trajectory: the kernels' shares and the roofline
+    lib.odwf_profile_enable(1)
+    traj()
+    torch.cuda.synchronize()
+    prof = read_profile(lib)
+    lib.odwf_profile_enable(0)
+    peak, peak_kind = measured_peaks()
+    kernels = {}
+    prof_total = sum(e["total_ms"] for e in prof) or 1.0
+    for e in prof:
+        tot = e["system_launches"] * e["bytes_per_system"] + e["launches"] * e["bytes_per_launch"]
+        kernels[e["name"]] = {"launches": e["launches"], "ms": round(e["total_ms"], 3),
+                              "share_of_profiled": round(e["total_ms"] / prof_total, 4),
+                              "gbs": round(tot / (e["total_ms"] / 1e3) / 1e9, 1) if e["total_ms"] > 0 else 0.0}
+    dom = max(prof, key=lambda e: e["total_ms"])
+    per_launch = (dom["system_launches"] * dom["bytes_per_system"] + dom["launches"] * dom["bytes_per_launch"]) \
+        / dom["launches"]
+    achieved = per_launch / (dom["total_ms"] / dom["launches"] / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "share_of_profiled": round(dom["total_ms"] / prof_total, 4),
+            "timing": "the library's per-launch CUDA events over one extra trajectory segment",
+            "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)"}
+    fc = next((e for e in prof if e["name"] == "pf.force_contract"), None)
+    force_alu = None
+    if fc:
+        links = 4 * V
+        flops = links * (672.0 * ns + 432.0)
+        ach = flops / (fc["total_ms"] / fc["launches"] / 1e3) / 1e12
+        force_alu = {"bound": "alu", "kernel": "pf.force_contract", "achieved": round(ach, 4),
+                     "peak": round(FP64_ALU_TFLOPS, 3), "unit": "TFLOP/s (FP64)",
+                     "frac": round(ach / FP64_ALU_TFLOPS, 4), "flops_per_link": 672 * ns + 432,
+                     "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz (nominal FP64 1.25 TFLOP/s)"}
+    h.close()
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        spi, cores = oracle_seconds_per_iteration(U0.cpu().numpy(), w, terms[1][0].cpu().numpy(), HMC_CHAIN[1])
+        it = float(np.mean(iters))
+        cpu = {"value": round(HMC_NSTEPS / (spi * it), 6), "unit": "MD steps/s", "cores": cores, "kind": "oracle",
+               "sample": "one FP64 oracle S^dag S CG iteration on this 16^3x32x16 field (m = 0.01; %.2f s on %d "
+                         "threads), times the %d inner iterations of one GPU trajectory segment (the oracle's "
+                         "force contractions, operator pieces and gauge force not counted)" % (spi, cores, it)}
+
+    ms_avg = sum(ms) / len(ms)
+    flops = float(np.mean(iters)) * (V // 2) * ns * 4 * 1420
+    if rank == 0:
+        line = {
+            "metric": "two-flavour HMC molecular-dynamics steps/s (Omelyan + Sexton-Weingarten, Wilson gauge + 3 "
+                      "mass-preconditioned pseudofermion ratios) on 16^3x32x16",
+            "value": round(value, 4), "unit": "MD steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_avg, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "%s solves, FP64 forces and updates" % args.prec, "data": "synthetic",
+            "config": {"workload": HMC_WORKLOAD, "lattice": "16^3x32", "Ns": ns, "m0": M0, "beta": HMC_BETA,
+                       "mass_chain": list(HMC_CHAIN), "tau": HMC_TAU, "md_steps_per_bench_step": HMC_NSTEPS,
+                       "integrator": "Omelyan, Sexton-Weingarten with %d gauge steps per outer drift" % HMC_INNER,
+                       "solves_per_bench_step": 3 * (2 + 2 * HMC_NSTEPS), "tol": TOL,
+                       "gauge": "U = exp(%g i H), H Gaussian traceless Hermitian (seed %d)" % (EPS, 21 + rank),
+                       "phi": "Gaussian even-site fields (seeds 23-25)", "P": "Gaussian momenta (seed 22)",
+                       "l2": "not flushed: every solve streams the 5D fields (%.0f MB each in FP16) many times "
+                             "over" % (V // 2 * ns * 52 / 1e6),
+                       "parallelism": "replicas only" if world > 1 else "single GPU"},
+            "cg_iters_per_step": iters, "dH": dH, "worst_true_resid": max(res),
+            "sustained_gflops": round(flops / (ms_avg / 1e3) / 1e9, 1),
+            "context": "the paper's first two-flavour DWF HMC on this lattice sustained ~150 GFLOP/s on one "
+                       "GTX-280 (Sec. 5; another machine and flop convention)",
+            "roofline": roof, "force_roofline": force_alu, "kernels": kernels, "cpu_baseline": cpu,
+            "gpu_launches": int(launches), "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
 SERVE_LATTICES = [(8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 48), (32, 32, 32, 32)]
 
 
@@ -1056,9 +1201,10 @@ def main():
     ap.add_argument("--delta", type=float, default=0.01, help="reliable-update threshold")
     ap.add_argument("--link-recon", type=int, default=12, choices=[12, 18])
     ap.add_argument("--check-every", type=int, default=8, help="iterations between host polls of the solver state")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "serve", "profile", "mres", "dslash", "flow"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "serve", "profile", "mres", "dslash", "flow", "hmc"],
                     help="c2: the default line; c3: 36-system batch on 24^3x48; c5: one 64^4 solve; serve; "
-                         "profile: a fixed short solver run for ncu; flow: gradient flow on 64^4")
+                         "profile: a fixed short solver run for ncu; flow: gradient flow on 64^4; hmc: two-flavour "
+                         "HMC molecular dynamics on 16^3x32x16")
     ap.add_argument("--dims", type=int, nargs=4, default=list(DIMS), help="profile: lattice")
     ap.add_argument("--ns", type=int, default=NS, help="profile: Ns")
     ap.add_argument("--nsys", type=int, default=3, help="profile: systems")
@@ -1095,6 +1241,8 @@ def main():
         run_residual_mass(args, world, rank, local)
     elif args.workload == "flow":
         run_flow(args, world, rank, local)
+    elif args.workload == "hmc":
+        run_hmc(args, world, rank, local)
     elif args.workload == "dslash":
         import torch
 

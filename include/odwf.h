@@ -367,6 +367,17 @@ int odwf_pf_force(odwf_handle* h, const void* phi, double m1, double m2, const o
                   double* action, void* force, odwf_solve_stats* stats, void* stream);
 
 /*
+ * Heat bath of the pseudofermion field of odwf_pf_force (Sec. 2's two-flavour parts): for a
+ * Gaussian eta (even-site field, host or device, SCHUR_EVEN layout, components with
+ * <|eta_i|^2> = 1), phi = S(m2)^-1 S(m1)^+ eta, so that S_pf(phi) = |eta|^2 and phi is distributed
+ * as exp(-S_pf).  S(m2) phi = S(m1)^+ eta is solved as (S(m2)^+ S(m2)) phi = S(m2)^+ S(m1)^+ eta by
+ * the library's CG with `params` (system and mq set here); its statistics go to stats (may be
+ * NULL).  phi: output, host or device, SCHUR_EVEN layout.  Synchronises `stream`.
+ */
+int odwf_pf_heatbath(odwf_handle* h, const void* eta, double m1, double m2, const odwf_solve_params* params,
+                     void* phi, odwf_solve_stats* stats, void* stream);
+
+/*
  * Wilson plaquette gauge action and force (Sec. 2: the gauge action of the HMC at beta = 6/g0^2).
  * U: gauge field (host or device, complex128, [mu][t][z][y][x][3][3], the layout of
  * odwf_set_gauge; need not be the handle's field, which this call leaves unchanged).
@@ -388,18 +399,24 @@ int odwf_gauge_force(odwf_handle* h, const void* U, double beta, double* action,
  * integrator 1: Omelyan (minimum norm, second order, lambda = 0.1931833275037836),
  *   P += lambda eps/2 Pi, U <- exp(eps/2 P) U, P += (1 - 2 lambda) eps/2 Pi, U <- exp(eps/2 P) U,
  *   P += lambda eps/2 Pi.
+ * n_inner 0: one time scale, Pi the total force.  n_inner >= 1 (Sexton-Weingarten multiple time
+ *   scales): the steps above kick with the pseudofermion forces alone, and each of their drifts
+ *   U <- exp(h P) U is replaced by n_inner steps of the same integrator over time h under the
+ *   gauge force alone (no solve on the inner scale).
  * U, P: device memory, complex128, gauge layout; updated in place.  P traceless anti-Hermitian.
  * phi[i] (host or device, SCHUR_EVEN layout), m1[i], m2[i] (host): 0 <= nterms <= 16 pseudofermion
  * terms; every solve runs with `params` (system and mq set per term).  energies (host, 2): H at
- * the start and at the end.  The handle's gauge field is replaced by U at every force
+ * the start and at the end.  stats (may be NULL): iters and n_reliable summed over the
+ * trajectory's solves, the largest true_resid, the summed time_ms, the first non-OK status.  The handle's gauge field is replaced by U at every force
  * evaluation and holds the final U on return.  FP64 except the inner solves.  No accept/reject
  * step and no momentum refresh: the caller draws P and phi and decides.  Synchronises `stream`.
- * Errors: ODWF_EINVAL for null or host U/P, nterms out of range, nsteps < 0, non-finite tau
- * or beta, an unknown integrator or bad params; the solver's codes from the inner solves.
+ * Errors: ODWF_EINVAL for null or host U/P, nterms out of range, nsteps < 0, n_inner outside
+ * [0, 1000], non-finite tau or beta, an unknown integrator or bad params; the solver's codes from the inner solves.
  */
 int odwf_md_trajectory(odwf_handle* h, void* U, void* P, int nterms, const void* const* phi, const double* m1,
-                       const double* m2, double beta, double tau, int nsteps, int integrator,
-                       const odwf_solve_params* params, double* energies, void* stream);
+                       const double* m2, double beta, double tau, int nsteps, int integrator, int n_inner,
+                       const odwf_solve_params* params, double* energies, odwf_solve_stats* stats,
+                       void* stream);
 
 /*
  * Time one kernel of the production mixed-precision iteration on its own: kind 1..4 = the

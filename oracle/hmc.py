@@ -31,10 +31,13 @@ and for full-lattice fields Lf, Rf, d<Lf, W Rf>/deps = tr(T G) per link with
 boundary.  Pi = ta(G_total) since tr(T ta(G)) = Re tr(T G) for traceless anti-Hermitian T.
 
 Molecular dynamics: momenta P_mu(x) traceless anti-Hermitian, kinetic energy
-K = -sum tr(P^2), H = K + S; Hamilton's equations dU/dt = P U, dP/dt = Pi / 2.
+K = -sum tr(P^2), H = K + S; Hamilton's equations dU/dt = P U, dP/dt = Pi / 2.  Multiple time
+scales (Sexton-Weingarten, Sec. 2): the outer integrator kicks with the pseudofermion forces and
+each of its drifts is n_inner steps of the same integrator under the gauge force alone.
 Parity status: pinned by tests/test_oracle_hmc.py (central finite differences of both actions
 along all eight generators, the heat-bath identity S(phi(eta)) = |eta|^2, reversibility and
-second-order energy conservation of the integrators).
+second-order energy conservation of the integrators, and the two limits in which the nested
+integrator is a single-scale one: no pseudofermion term, and beta = 0).
 """
 from __future__ import annotations
 
@@ -178,4 +181,45 @@ def md_omelyan(U, P, eps, nsteps, terms, beta, lam=OMELYAN_LAMBDA):
         P = P + 0.5 * (1.0 - 2.0 * lam) * eps * _force_total(U, terms, beta)
         U = expm(0.5 * eps * P) @ U
         P = P + 0.5 * lam * eps * _force_total(U, terms, beta)
+    return U, P
+
+
+def _inner(U, P, h, n_inner, beta, integrator, lam):
+    """n_inner steps of the integrator over time h under the gauge force alone."""
+    d = h / n_inner
+    for _ in range(n_inner):
+        if integrator == "omelyan":
+            P = P + 0.5 * lam * d * gauge_force(U, beta)
+            U = expm(0.5 * d * P) @ U
+            P = P + 0.5 * (1.0 - 2.0 * lam) * d * gauge_force(U, beta)
+            U = expm(0.5 * d * P) @ U
+            P = P + 0.5 * lam * d * gauge_force(U, beta)
+        else:
+            P = P + 0.25 * d * gauge_force(U, beta)
+            U = expm(d * P) @ U
+            P = P + 0.25 * d * gauge_force(U, beta)
+    return U, P
+
+
+def md_nested(U, P, eps, nsteps, terms, beta, n_inner, integrator="omelyan", lam=OMELYAN_LAMBDA):
+    """Sexton-Weingarten multiple time scales: outer steps of size eps kick with the pseudofermion
+    forces only; every drift of the outer step (eps/2 twice for Omelyan, eps once for leapfrog)
+    is _inner over that time with the gauge force."""
+    U = U.copy()
+    P = P.copy()
+
+    def ff(U):
+        return _force_total(U, terms, 0.0)
+
+    for _ in range(nsteps):
+        if integrator == "omelyan":
+            P = P + 0.5 * lam * eps * ff(U)
+            U, P = _inner(U, P, 0.5 * eps, n_inner, beta, integrator, lam)
+            P = P + 0.5 * (1.0 - 2.0 * lam) * eps * ff(U)
+            U, P = _inner(U, P, 0.5 * eps, n_inner, beta, integrator, lam)
+            P = P + 0.5 * lam * eps * ff(U)
+        else:
+            P = P + 0.25 * eps * ff(U)
+            U, P = _inner(U, P, eps, n_inner, beta, integrator, lam)
+            P = P + 0.25 * eps * ff(U)
     return U, P

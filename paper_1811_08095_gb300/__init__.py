@@ -269,6 +269,40 @@ class Handle:
                                       ptr(force), ctypes.byref(st), stream_ptr(stream)))
         return act.value, _stats_dict(st)
 
+    def pf_heatbath(self, eta, m1, m2, phi, tol=1e-10, max_iter=100000, prec="f64", updates="auto", stream=None):
+        """odwf_pf_heatbath: phi = S(m2)^-1 S(m1)^+ eta into `phi` (an even-site buffer); returns the
+        solve's stats dict."""
+        p = _params(tol, max_iter, prec, 0.01, ODWF_SYS_SCHUR_NORMAL, 12, None, 8, "f32", updates)
+        st = _lib.odwf_solve_stats()
+        check(self._lib.odwf_pf_heatbath(self._h, ptr(eta), float(m1), float(m2), ctypes.byref(p), ptr(phi),
+                                         ctypes.byref(st), stream_ptr(stream)))
+        return _stats_dict(st)
+
+    def hmc_trajectory(self, U, P, etas, masses, beta, tau, nsteps, u, integrator="omelyan", n_inner=0, tol=1e-10,
+                       prec="f16", stream=None):
+        """One HMC trajectory (Sec. 2).  The caller draws the momenta P (device, traceless
+        anti-Hermitian), one Gaussian even-site field per pseudofermion term in etas (device),
+        and u uniform in [0, 1).  Heat bath phi_i = S(m2_i)^-1 S(m1_i)^+ eta_i for masses =
+        [(m1_i, m2_i), ...], the molecular dynamics of odwf_md_trajectory, then the Metropolis
+        test u < exp(-dH); a rejected trajectory leaves U as it was.  Returns (accepted, dH)."""
+        import math
+
+        self.set_gauge(U, stream=stream)
+        phis = []
+        for eta, (m1, m2) in zip(etas, masses):
+            phi = eta.new_empty(eta.shape)
+            self.pf_heatbath(eta, m1, m2, phi, tol=tol, prec=prec, stream=stream)
+            phis.append(phi)
+        U0 = U.clone()
+        h0, h1, _ = self.md_trajectory(U, P, [(phi, m1, m2) for phi, (m1, m2) in zip(phis, masses)], beta, tau,
+                                       nsteps, integrator, n_inner=n_inner, tol=tol, prec=prec, stream=stream)
+        dH = h1 - h0
+        accepted = dH <= 0.0 or u < math.exp(-dH)
+        if not accepted:
+            U.copy_(U0)
+            self.set_gauge(U, stream=stream)
+        return accepted, dH
+
     def gauge_force(self, U, beta, force=None, stream=None):
         """odwf_gauge_force: the Wilson plaquette action of U (host array or device tensor of the
         gauge field's shape) and, when `force` is given, its force Pi into it.  Returns the action."""
@@ -277,10 +311,12 @@ class Handle:
                                          stream_ptr(stream)))
         return act.value
 
-    def md_trajectory(self, U, P, terms, beta, tau, nsteps, integrator="omelyan", tol=1e-10, max_iter=100000,
-                      prec="f64", updates="auto", stream=None):
+    def md_trajectory(self, U, P, terms, beta, tau, nsteps, integrator="omelyan", n_inner=0, tol=1e-10,
+                      max_iter=100000, prec="f64", updates="auto", stream=None):
         """odwf_md_trajectory: integrate (U, P) (device tensors, updated in place) over time tau in
-        nsteps steps; terms = [(phi, m1, m2), ...].  Returns (H_start, H_end)."""
+        nsteps steps; terms = [(phi, m1, m2), ...]; n_inner > 0: the gauge force on an inner time
+        scale of n_inner steps per drift (Sexton-Weingarten).  Returns (H_start, H_end, stats
+        dict of the trajectory's solves)."""
         n = len(terms)
         integ = {"leapfrog": 0, "omelyan": 1}[integrator]
         p = _params(tol, max_iter, prec, 0.01, ODWF_SYS_SCHUR_NORMAL, 12, None, 8, "f32", updates)
@@ -288,10 +324,11 @@ class Handle:
         m1 = np.ascontiguousarray([t[1] for t in terms] or [0.0], dtype=np.float64)
         m2 = np.ascontiguousarray([t[2] for t in terms] or [0.0], dtype=np.float64)
         en = np.zeros(2, dtype=np.float64)
+        st = _lib.odwf_solve_stats()
         check(self._lib.odwf_md_trajectory(self._h, ptr(U), ptr(P), n, ctypes.cast(phis, ctypes.c_void_p), ptr(m1),
-                                           ptr(m2), float(beta), float(tau), int(nsteps), integ, ctypes.byref(p),
-                                           ptr(en), stream_ptr(stream)))
-        return float(en[0]), float(en[1])
+                                           ptr(m2), float(beta), float(tau), int(nsteps), integ, int(n_inner),
+                                           ctypes.byref(p), ptr(en), ctypes.byref(st), stream_ptr(stream)))
+        return float(en[0]), float(en[1]), _stats_dict(st)
 
     def residual_mass(self, site, tol=1e-10, max_iter=100000, prec="f64", mq=None, stream=None):
         """odwf_residual_mass at site (x, y, z, t): returns (m_res, C(t) array, stats dict)."""

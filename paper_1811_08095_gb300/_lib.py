@@ -117,8 +117,10 @@ _SIGS = {
     "serve_set_policy": ([P, D, I, I], I),
     "serve_cancel": ([P, ctypes.c_uint64], I),
     "odwf_pf_force": ([P, P, D, D, ctypes.POINTER(odwf_solve_params), ctypes.POINTER(D), P, P, P], I),
+    "odwf_pf_heatbath": ([P, P, D, D, ctypes.POINTER(odwf_solve_params), P, ctypes.POINTER(odwf_solve_stats), P], I),
     "odwf_gauge_force": ([P, P, D, ctypes.POINTER(D), P, P], I),
-    "odwf_md_trajectory": ([P, P, P, I, P, P, P, D, D, I, I, ctypes.POINTER(odwf_solve_params), P, P], I),
+    "odwf_md_trajectory": ([P, P, P, I, P, P, P, D, D, I, I, I, ctypes.POINTER(odwf_solve_params), P,
+                            ctypes.POINTER(odwf_solve_stats), P], I),
     "odwf_flow_create": ([ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(P)], I),
     "odwf_flow_destroy": ([P], I),
     "odwf_flow_set_gauge": ([P, P, P], I),

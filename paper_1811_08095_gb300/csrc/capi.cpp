@@ -182,6 +182,15 @@ int odwf_pf_force(odwf_handle* h, const void* phi, double m1, double m2, const o
     GUARD_END
 }
 
+int odwf_pf_heatbath(odwf_handle* h, const void* eta, double m1, double m2, const odwf_solve_params* params,
+                     void* phi, odwf_solve_stats* stats, void* stream) {
+    GUARD_BEGIN
+    if (!h) return fail(ODWF_EINVAL, "odwf_pf_heatbath: null handle");
+    ON_DEVICE(h, "odwf_pf_heatbath", eta, phi);
+    WITH_BOUNDS(h, h->e.pf_heatbath(eta, m1, m2, params, phi, stats, (cudaStream_t)stream), stream);
+    GUARD_END
+}
+
 int odwf_gauge_force(odwf_handle* h, const void* U, double beta, double* action, void* force, void* stream) {
     GUARD_BEGIN
     if (!h) return fail(ODWF_EINVAL, "odwf_gauge_force: null handle");
@@ -191,15 +200,16 @@ int odwf_gauge_force(odwf_handle* h, const void* U, double beta, double* action,
 }
 
 int odwf_md_trajectory(odwf_handle* h, void* U, void* P, int nterms, const void* const* phi, const double* m1,
-                       const double* m2, double beta, double tau, int nsteps, int integrator,
-                       const odwf_solve_params* params, double* energies, void* stream) {
+                       const double* m2, double beta, double tau, int nsteps, int integrator, int n_inner,
+                       const odwf_solve_params* params, double* energies, odwf_solve_stats* stats,
+                       void* stream) {
     GUARD_BEGIN
     if (!h) return fail(ODWF_EINVAL, "odwf_md_trajectory: null handle");
     ON_DEVICE(h, "odwf_md_trajectory", U, P);
     for (int i = 0; phi && i < nterms && i < 16; ++i) ON_DEVICE(h, "odwf_md_trajectory", phi[i]);
     WITH_BOUNDS(h,
-                h->e.md_trajectory(U, P, nterms, phi, m1, m2, beta, tau, nsteps, integrator, params, energies,
-                                   (cudaStream_t)stream),
+                h->e.md_trajectory(U, P, nterms, phi, m1, m2, beta, tau, nsteps, integrator, n_inner, params, energies,
+                                   stats, (cudaStream_t)stream),
                 stream);
     GUARD_END
 }

@@ -118,10 +118,12 @@ struct Engine {
     int gauge_force(const double2* U, double beta, double* action, double2* F, cudaStream_t st);
     int gauge_force_api(const void* U, double beta, double* action, void* force, cudaStream_t st);
     int md_trajectory(void* U, void* P, int nterms, const void* const* phi, const double* m1, const double* m2,
-                      double beta, double tau, int nsteps, int integrator, const odwf_solve_params* prm,
-                      double* energies, cudaStream_t st);
+                      double beta, double tau, int nsteps, int integrator, int n_inner,
+                      const odwf_solve_params* prm, double* energies, odwf_solve_stats* stats, cudaStream_t st);
     int pf_force(const void* phi, double m1, double m2, const odwf_solve_params* prm, double* action, void* force,
                  odwf_solve_stats* stats, cudaStream_t st);
+    int pf_heatbath(const void* eta, double m1, double m2, const odwf_solve_params* prm, void* phi,
+                    odwf_solve_stats* stats, cudaStream_t st);
     int apply_ff_normal(void* out, const void* in, cudaStream_t st);
     int apply_low_normal(void* out, const void* in, int prec, int recon, cudaStream_t st);
     int mixed_cg_step(int prec, int recon, int link_prec, double mq_step, const void* p_prev, const void* r, const void* x,

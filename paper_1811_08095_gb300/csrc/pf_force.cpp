@@ -13,6 +13,7 @@
 #include <cmath>
 
 #include "engine.h"
+#include "profile.h"
 
 namespace odwf {
 
@@ -109,12 +110,20 @@ int Engine::pf_force(const void* phi, double m1, double m2, const odwf_solve_par
         double2* G = (double2*)get_ws("pf.G", gb, &rc);
         if (rc) return rc;
         // 2 Re<X, dS2 phi>: weight 2 x 1/2; then -2 Re<Y, dS1 X>
+        // algorithmic bytes per link: four spinors per s, the link, G in and out
+        const double cbytes = 8.0 * (double)vh() * (4.0 * ns * 192 + 144 + 2 * 144);
         if ((rc = term_fields(this, X, Phi, r2, Le, Lo, Re, Ro, T, st))) return rc;
-        ODWF_CK(launch_force_contract(g, ns, links_d18, Le.ref_sys(0), Lo.ref_sys(0), Re.ref_sys(0), Ro.ref_sys(0), 1.0,
-                                      G, false, st));
+        {
+            ProfScope ps("pf.force_contract", cbytes, st);
+            ODWF_CK(launch_force_contract(g, ns, links_d18, Le.ref_sys(0), Lo.ref_sys(0), Re.ref_sys(0), Ro.ref_sys(0),
+                                          1.0, G, false, st));
+        }
         if ((rc = term_fields(this, Y, X, r1, Le, Lo, Re, Ro, T, st))) return rc;
-        ODWF_CK(launch_force_contract(g, ns, links_d18, Le.ref_sys(0), Lo.ref_sys(0), Re.ref_sys(0), Ro.ref_sys(0), -1.0,
-                                      G, true, st));
+        {
+            ProfScope ps("pf.force_contract", cbytes, st);
+            ODWF_CK(launch_force_contract(g, ns, links_d18, Le.ref_sys(0), Lo.ref_sys(0), Re.ref_sys(0), Ro.ref_sys(0),
+                                          -1.0, G, true, st));
+        }
         const size_t fb = (size_t)8 * vh() * 9 * sizeof(double2);
         const bool fdev = is_device_ptr(force);
         double2* fout = fdev ? (double2*)force : (double2*)get_ws("pf.fext", fb, &rc);
@@ -122,6 +131,45 @@ int Engine::pf_force(const void* phi, double m1, double m2, const odwf_solve_par
         ODWF_CK(launch_force_finalize(g, G, fout, st));
         if (!fdev) ODWF_CK(cudaMemcpyAsync(force, fout, fb, cudaMemcpyDeviceToHost, st));
     }
+    ODWF_CK(cudaStreamSynchronize(st));
+    return ODWF_OK;
+}
+
+// Heat bath of the two-flavour ratio: phi = S2^-1 S1^+ eta gives S_pf(phi) = |eta|^2 for a
+// Gaussian eta, i.e. phi drawn from exp(-S_pf).  S2 phi = S1^+ eta is solved through the normal
+// equations, phi = (S2^+ S2)^-1 S2^+ S1^+ eta, by the library's CG at m2.
+int Engine::pf_heatbath(const void* eta, double m1, double m2, const odwf_solve_params* prm, void* phi,
+                        odwf_solve_stats* stats, cudaStream_t st) {
+    if (!gauge_set) return fail(ODWF_EINVAL, "odwf_pf_heatbath: gauge field not set");
+    if (!eta || !phi) return fail(ODWF_EINVAL, "odwf_pf_heatbath: null eta or phi");
+    if (!std::isfinite(m1) || !std::isfinite(m2)) return fail(ODWF_EINVAL, "odwf_pf_heatbath: non-finite mass");
+    int rc = check_params(prm);
+    if (rc) return rc;
+    const size_t eb = ext_bytes(ODWF_MODE_SCHUR_EVEN);
+    const double2* deta = nullptr;
+    if ((rc = stage_phi(this, eta, eb, st, &deta))) return rc;
+    double* r = (double*)get_ws("pf.r", 2 * sizeof(double), &rc);
+    if (rc) return rc;
+    const double rv[2] = {m1 / (2.0 * m0), m2 / (2.0 * m0)};
+    ODWF_CK(cudaMemcpyAsync(r, rv, sizeof(rv), cudaMemcpyHostToDevice, st));
+    ODWF_CK(cudaStreamSynchronize(st));  // rv lives on this stack frame
+    HalfField E, T;
+    if ((rc = alloc_half("pf.phi", Sp::F64, 1, &E)) || (rc = alloc_half("pf.psi", Sp::F64, 1, &T))) return rc;
+    ODWF_CK(launch_pack(Sp::F64, deta, E.ref_sys(0), g, 0, ns, 1, st));
+    if ((rc = apply_schur64(E, T, true, r, st))) return rc;      // S1^+ eta
+    if ((rc = apply_schur64(T, E, true, r + 1, st))) return rc;  // S2^+ S1^+ eta
+    double2* bext = (double2*)get_ws("pf.bext", eb, &rc);
+    if (rc) return rc;
+    ODWF_CK(launch_unpack(Sp::F64, E.ref_sys(0), bext, g, 0, ns, 1, st));
+    odwf_solve_params p2 = *prm;
+    p2.system = ODWF_SYS_SCHUR_NORMAL;
+    p2.mq = m2;
+    void* xs[1] = {phi};
+    const void* bs[1] = {bext};
+    odwf_solve_stats s2{};
+    rc = solve(1, xs, bs, &m2, &p2, &s2, st);
+    if (stats) *stats = s2;
+    if (rc) return rc;
     ODWF_CK(cudaStreamSynchronize(st));
     return ODWF_OK;
 }

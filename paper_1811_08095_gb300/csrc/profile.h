@@ -28,6 +28,19 @@ ProfSlot prof_begin(int cls, cudaStream_t s);
 void prof_end(const ProfSlot& slot, cudaStream_t s);
 void prof_collect();  // after a stream synchronize: accumulate finished event pairs
 
+// Scoped per-launch timing of one kernel class with its algorithmic bytes per launch (a no-op
+// when profiling is off); the launcher counts the launch itself.
+struct ProfScope {
+    ProfSlot slot;
+    cudaStream_t st;
+    ProfScope(const char* name, double bytes_per_launch, cudaStream_t s) : st(s) {
+        slot = prof_begin(prof_enabled() ? prof_class(name, 0.0, bytes_per_launch) : -1, s);
+    }
+    ~ProfScope() { prof_end(slot, st); }
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+};
+
 // NVTX range for the solver's host-side phases (iteration chunks, reliable updates, admission,
 // finalization, serving passes): visible in Nsight tools, a no-op without one.
 struct NvtxRange {

@@ -7,7 +7,11 @@ the molecular-dynamics integrators (oracle/hmc.py) against facts fixed outside t
   boundaries; the same for the Wilson gauge action at beta = 6.2;
 * the heat-bath field phi = S2^-1 S1^+ eta has S_pf(phi) = |eta|^2;
 * leapfrog and Omelyan steps are reversible, conserve H to second order in the step, and Omelyan
-  violates it less than leapfrog at the same step.
+  violates it less than leapfrog at the same step;
+* the nested (Sexton-Weingarten) integrator is a single-scale one in its two limits: without
+  pseudofermion terms it is 2 n_inner (Omelyan) or n_inner (leapfrog) gauge steps per outer
+  step, and at beta = 0 its inner drifts compose to the outer drift (exp(aP) exp(bP) =
+  exp((a + b) P)); it is reversible and second order.
 """
 import numpy as np
 import pytest
@@ -113,3 +117,38 @@ def test_md_conserves_energy_to_second_order(oracle_lib):
         r = dH[name][0] / dH[name][1]
         assert 3.0 < r < 5.5, (name, dH[name], r)
     assert dH["omelyan"][1] < 0.5 * dH["leapfrog"][1], dH
+
+
+@pytest.mark.parametrize("integrator", ["leapfrog", "omelyan"])
+def test_nested_integrator_limits(oracle_lib, integrator):
+    dims, ns = (2, 2, 2, 4), 4
+    U, w = _case(dims, ns, seed=14, eps=0.4)
+    P = syn.gaussian_momenta(dims, 15)
+    single = hmc.md_leapfrog if integrator == "leapfrog" else hmc.md_omelyan
+    k = 1 if integrator == "leapfrog" else 2
+    # gauge only: the inner integrator alone, n_inner (x2 for Omelyan's two drifts) per outer step
+    U1, P1 = hmc.md_nested(U, P, 0.08, 2, [], 6.2, 3, integrator)
+    U2, P2 = single(U, P, 0.08 / (k * 3), 2 * k * 3, [], 6.2)
+    assert np.abs(U1 - U2).max() < 1e-13 and np.abs(P1 - P2).max() < 1e-12
+    # no gauge force: the inner drifts compose to the outer one
+    terms = _terms(U, ns, w)
+    U1, P1 = hmc.md_nested(U, P, 0.05, 2, terms, 0.0, 3, integrator)
+    U2, P2 = single(U, P, 0.05, 2, terms, 0.0)
+    assert np.abs(U1 - U2).max() < 1e-12 and np.abs(P1 - P2).max() < 1e-10
+    assert np.abs(U1 - U).max() > 1e-2
+
+
+def test_nested_integrator_is_reversible_and_second_order(oracle_lib):
+    dims, ns = (2, 2, 2, 4), 4
+    U, w = _case(dims, ns, seed=10, eps=0.3)
+    P = syn.gaussian_momenta(dims, 13)
+    terms = _terms(U, ns, w)
+    U1, P1 = hmc.md_nested(U, P, 0.05, 3, terms, 6.2, 2)
+    U2, P2 = hmc.md_nested(U1, -P1, 0.05, 3, terms, 6.2, 2)
+    assert np.abs(U2 - U).max() < 1e-9 and np.abs(P2 + P).max() < 1e-9
+    H0 = hmc.hamiltonian(U, P, terms, 6.2)
+    dH = []
+    for n in (16, 32):
+        U1, P1 = hmc.md_nested(U, P, 0.2 / n, n, terms, 6.2, 2)
+        dH.append(abs(hmc.hamiltonian(U1, P1, terms, 6.2) - H0))
+    assert 3.0 < dH[0] / dH[1] < 5.5, dH
