@@ -4,7 +4,7 @@
 One step solves the 16^3 x 32 x Ns=16 workload's three systems (m_q = 0.002, 0.04, 0.5,
 one Gaussian right-hand side each) to a true residual of 1e-10 with the batched mixed-
 precision CG (FP16 storage with per-site scales, FP32 links of 12 reals, FP32 arithmetic,
-FP64 reliable updates), as one odwf_cg_solve_batched call.  Prints one JSON line.
+float-float reliable updates), as one odwf_cg_solve_batched call.  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--prec f16|bf16|f32]
 
@@ -194,6 +194,11 @@ def ncu_traffic(kernel_class):
     return None
 
 
+def update_arith_name(updates):
+    """The reliable-update arithmetic of a mixed solve (AUTO is float-float)."""
+    return "FP64" if updates == "f64" else "float-float"
+
+
 def aggregate(t_local_s: float, solves_local: int, dist=None, device=None):
     """Whole-job throughput of independent replicas: every rank's solves over the slowest rank's
     timed region (max over ranks), as the replicas-only multi-GPU contract asks."""
@@ -312,7 +317,8 @@ def run_ours(args, world, rank, local):
 
     def step(prec):
         return h.cg_solve_batched(xs, bs, list(MASSES), tol=TOL, max_iter=200000, prec=prec, delta=args.delta,
-                                  link_recon=args.link_recon, check_every=args.check_every, stream=stream)
+                                  link_recon=args.link_recon, check_every=args.check_every, stream=stream,
+                                  updates=args.updates)
 
     for _ in range(args.warmup):
         stats = step(args.prec)
@@ -405,13 +411,14 @@ def run_ours(args, world, rank, local):
     h2d = sum(b.numel() * b.element_size() for b in bh)
     d2h = sum(x.numel() * x.element_size() for x in xh)
     h.cg_solve_batched([x.numpy() for x in xh], [b.numpy() for b in bh], list(MASSES), tol=TOL, max_iter=200000,
-                       prec=args.prec, delta=args.delta, link_recon=args.link_recon, stream=stream)  # warm
+                       prec=args.prec, delta=args.delta, link_recon=args.link_recon, stream=stream,
+                       updates=args.updates)  # warm
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         h.cg_solve_batched([x.numpy() for x in xh], [b.numpy() for b in bh], list(MASSES), tol=TOL,
                            max_iter=200000, prec=args.prec, delta=args.delta, link_recon=args.link_recon,
-                           stream=stream)
+                           stream=stream, updates=args.updates)
     e2e_s = time.perf_counter() - t0
     e2e = {"value": round(len(MASSES) * args.steps * world / e2e_s, 4), "unit": "solves/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
@@ -470,8 +477,9 @@ def run_ours(args, world, rank, local):
                        "gauge": "U = exp(0.25 i H), H Gaussian traceless Hermitian (seed 2)",
                        "omega": "shifted (R5) Zolotarev on [0.05, 6.2]", "tol": TOL,
                        "precision": "%s storage (per-site FP32 scale), FP32 links (%d reals), FP32 arithmetic, "
-                                    "FP64 reliable updates (delta %g) and reductions" % (args.prec, args.link_recon,
-                                                                                        args.delta),
+                                    "%s reliable updates (delta %g), FP64 reductions" % (
+                                        args.prec, args.link_recon, update_arith_name(args.updates),
+                                        args.delta),
                        "solver": "batched even-odd CG on S^dag S, 3 systems per launch",
                        "l2": "flushed between steps (512 MB write); per-system working set > 1 GB",
                        "parallelism": "replicas only" if world > 1 else "single GPU",
@@ -958,7 +966,7 @@ def run_batched_c3(args, world, rank, local):
 
     def step(prec, xs_, bs_, mqs_):
         return h.cg_solve_batched(xs_, bs_, mqs_, tol=TOL, max_iter=200000, prec=prec, delta=args.delta,
-                                  link_recon=args.link_recon, stream=stream)
+                                  link_recon=args.link_recon, stream=stream, updates=args.updates)
 
     for _ in range(args.warmup):
         step(args.prec, xs, bs, mqs)
@@ -1011,7 +1019,7 @@ def run_batched_c3(args, world, rank, local):
 
 def run_paper_scale_c5(args, world, rank, local):
     """64^4 x Ns=16, m_q = 0.002, links exp(0.2 i H) seed 5 stored as FP32 12-real, BF16 inner
-    solve with FP64 reliable updates, one Gaussian right-hand side (seed 5), one solve per
+    solve with float-float reliable updates, one Gaussian right-hand side (seed 5), one solve per
     step.  Reports the solve time, iterations, true residual and the device memory used."""
     import torch
 
@@ -1044,7 +1052,8 @@ def run_paper_scale_c5(args, world, rank, local):
         if i >= args.warmup:
             clocks.start()
         e0.record(stream)
-        st = h.cg_solve(x, b, tol=TOL, max_iter=200000, prec=prec, delta=args.delta, link_recon=12, stream=stream)
+        st = h.cg_solve(x, b, tol=TOL, max_iter=200000, prec=prec, delta=args.delta, link_recon=12, stream=stream,
+                        updates=args.updates)
         e1.record(stream)
         e1.synchronize()
         if i >= args.warmup:
@@ -1200,6 +1209,8 @@ def main():
     ap.add_argument("--prec", default="f16", choices=["f16", "bf16", "f32"])
     ap.add_argument("--delta", type=float, default=0.01, help="reliable-update threshold")
     ap.add_argument("--link-recon", type=int, default=12, choices=[12, 18])
+    ap.add_argument("--updates", default="auto", choices=["auto", "f64", "ff"],
+                    help="arithmetic of the reliable updates (auto: the library's choice)")
     ap.add_argument("--check-every", type=int, default=8, help="iterations between host polls of the solver state")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "serve", "profile", "mres", "dslash", "flow", "hmc"],
                     help="c2: the default line; c3: 36-system batch on 24^3x48; c5: one 64^4 solve; serve; "

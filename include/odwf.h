@@ -109,13 +109,11 @@ typedef struct {
                            (24 bytes per link, no scale: SU(3) entries have modulus <= 1; needs
                            Ns = 8 or 16 and link_recon 0 or 12) */
     int32_t update_arith; /* mixed: arithmetic of the reliable updates (true residual b - A x) and of
-                           the accumulated solution.  ODWF_UPDATES_AUTO (0): float-float for a solve
-                           of one system, FP64 for batches; ODWF_UPDATES_F64: FP64;
-                           ODWF_UPDATES_FF: float-float (pairs of FP32, about 48 bits, on the FP32
-                           pipe).  Both resolve the true residual far below 1e-10.  Float-float is
-                           faster when the update is on the critical path (one system); in a batch
-                           the FP64 pipe runs beside the FP32-bound iterations of the other systems,
-                           where float-float competes with them for the FP32 pipe.  Full-lattice
+                           the accumulated solution.  ODWF_UPDATES_AUTO (0) and ODWF_UPDATES_FF:
+                           float-float (pairs of FP32, about 48 bits, on the FP32 pipe);
+                           ODWF_UPDATES_F64: FP64.  Both resolve the true residual far below 1e-10;
+                           on GB300, whose FP64 rate is a small fraction of its FP32 rate,
+                           float-float is faster for one system and for batches.  Full-lattice
                            systems (FULL_NORMAL, FULL_DIRAC) always update in FP64. */
 } odwf_solve_params;
 

@@ -61,6 +61,7 @@ struct BatchCG {
     SysState* st_host = nullptr;   // pinned mirror
     double* r_dev = nullptr;       // device [cap]
     double* partials = nullptr;    // device [cap * nblk]
+    int nblk = 0;                  // partials per system (every reducing launch's grid fits)
     unsigned* counters = nullptr;  // device [cap]
     // reliable updates run on their own stream, overlapping the other systems' iterations
     cudaStream_t s_rel = nullptr;

@@ -88,7 +88,8 @@ struct HopParams {
     int gate;                   // 1: run only systems whose st[sys].status == need_status
     int need_status;
     SysState* st;               // per-system scalars (gate / norm / cg / resid)
-    double* partials;           // [sys][gridDim.x]
+    double* partials;           // [sys][part_stride] (part_stride 0: gridDim.x)
+    int part_stride;            // partials per system, fixed for every launch of one batch
     unsigned* counters;         // [sys]
     int sys_base;               // system index offset (blockIdx.y + sys_base)
     unsigned long long* prof_count;  // optional: counts running (system, launch) pairs
@@ -192,6 +193,42 @@ __device__ __forceinline__ void su3_mul(const R u[18], const R h[12], R w[12], b
         }
 }
 
+// Float-float instance: each output component is a six-term dot product, summed as a compensated
+// dot product (two-product of the leading parts plus the cross terms, two-sum of the running
+// total, the rounding errors gathered in a second word and added once at the end), as accurate as
+// the float-float operators of ff.cuh with about two thirds of their FP32 operations.
+__device__ __forceinline__ void ff_dot_acc(float& s, float& c, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = fmaf(ah, bh, -p);  // ah bh - p, exact
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    const float t = __fadd_rn(s, p);
+    const float bb = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb));  // s + p - t, exact
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(err, e));
+}
+__device__ __forceinline__ void su3_mul(const ff u[18], const ff h[12], ff w[12], bool dag) {
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float rs = 0.f, rc = 0.f, is = 0.f, ic = 0.f;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const int ix = dag ? (3 * b + a) : (3 * a + b);
+                const ff ur = u[2 * ix], ui = dag ? -u[2 * ix + 1] : u[2 * ix + 1];
+                const ff hr = h[6 * sp + 2 * b], hi = h[6 * sp + 2 * b + 1];
+                ff_dot_acc(rs, rc, ur.hi, ur.lo, hr.hi, hr.lo);
+                ff_dot_acc(rs, rc, -ui.hi, -ui.lo, hi.hi, hi.lo);
+                ff_dot_acc(is, ic, ur.hi, ur.lo, hi.hi, hi.lo);
+                ff_dot_acc(is, ic, ui.hi, ui.lo, hr.hi, hr.lo);
+            }
+            w[6 * sp + 2 * a] = ff_fast_two_sum(rs, rc);
+            w[6 * sp + 2 * a + 1] = ff_fast_two_sum(is, ic);
+        }
+}
+
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -265,9 +302,12 @@ __device__ __forceinline__ void finalize_scalar(SysState* st, double total, int 
 // leave and warp 0 alone writes the partial and, in the last block, sums all partials.  The sum
 // order is fixed whatever block finishes last, so results are deterministic.  Must be the
 // kernel's last statement (warps other than 0 return here).
+// System sys's partials start at sys * part_stride (part_stride >= every grid's block count, the same
+// for every launch of a batch, so that launches of different block counts for different systems can
+// run concurrently); part_stride 0 means gridDim.x.
 template <class R>
 __device__ __forceinline__ void reduce_and_finalize(R v, double* partials, unsigned* counters, SysState* st,
-                                                    int sys, int fin) {
+                                                    int sys, int fin, int part_stride) {
     __shared__ double sm[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     v = warp_sum(v);
@@ -277,7 +317,7 @@ __device__ __forceinline__ void reduce_and_finalize(R v, double* partials, unsig
     double bs = lane < nw ? sm[lane] : 0.0;
     bs = warp_sum(bs);
     const int nb = gridDim.x;
-    double* part = partials + (size_t)sys * nb;
+    double* part = partials + (size_t)sys * (size_t)(part_stride > 0 ? part_stride : nb);
     unsigned prev = 0;
     if (lane == 0) {
         part[blockIdx.x] = bs;
@@ -297,8 +337,10 @@ __device__ __forceinline__ void reduce_and_finalize(R v, double* partials, unsig
 }
 
 // ---------------------------------------------------------------- the fused hopping kernel
+// The body of the generic hop (one thread per 5D site); hop_kernel below launches it at 256
+// threads per block, other instances (float-float) at their own bounds.
 template <class SPin, class SPz, class SPout, class SPacc, class LK, class R, int F>
-__global__ void __launch_bounds__(256) hop_kernel(const HopParams<R> P) {
+__device__ __forceinline__ void hop_body(const HopParams<R>& P) {
     constexpr bool DAG = (F & F_DAG) != 0;
     constexpr int ZOP = (F & F_ZOP_MASK) >> F_ZOP_SHIFT;
     constexpr int HOPOP = (F & F_HOP_MASK) >> F_HOP_SHIFT;
@@ -435,7 +477,12 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams<R> P) {
         if (valid) SpinorIO<SPout, R>::store(P.out.d(sys), P.out.n(sys), (size_t)h, s, ns, res);
     }
 
-    if (REDUCE) reduce_and_finalize(nrm, P.partials, P.counters, P.st, sys, FIN);
+    if (REDUCE) reduce_and_finalize(nrm, P.partials, P.counters, P.st, sys, FIN, P.part_stride);
+}
+
+template <class SPin, class SPz, class SPout, class SPacc, class LK, class R, int F>
+__global__ void __launch_bounds__(256) hop_kernel(const HopParams<R> P) {
+    hop_body<SPin, SPz, SPout, SPacc, LK, R, F>(P);
 }
 
 // ---------------------------------------------------------------- site-local kernels
@@ -533,7 +580,7 @@ __global__ void __launch_bounds__(256) unpack_kernel(FieldRef in, double2* __res
 template <class SPx, class SPy, class R>
 __global__ void __launch_bounds__(256) vec_kernel(FieldRef x, FieldRef y, size_t n5, int ns, int kind, double coef,
                                                   SysState* st, int gate, int need, double* partials,
-                                                  unsigned* counters, int sys_base,
+                                                  unsigned* counters, int part_stride, int sys_base,
                                                   unsigned long long* prof_count) {
     const int sys = blockIdx.y + sys_base;
     if (gate && st[sys].status != need) return;
@@ -601,7 +648,7 @@ __global__ void __launch_bounds__(256) vec_kernel(FieldRef x, FieldRef y, size_t
             }
         }
     }
-    if (kind == 3) reduce_and_finalize<double>(nrm, partials, counters, st, sys, FIN_STORE);
+    if (kind == 3) reduce_and_finalize<double>(nrm, partials, counters, st, sys, FIN_STORE, part_stride);
 }
 
 }  // namespace odwf

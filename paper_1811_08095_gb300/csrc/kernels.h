@@ -7,6 +7,11 @@
 
 namespace odwf {
 
+// Reducing kernels write one partial per block and system; the buffer is sized for blocks of at
+// least this many threads, each thread one 5D site (or more).
+constexpr int kMinReduceBlock = 64;
+
+
 enum class Sp { F64 = 0, F32 = 1, F16 = 2, BF16 = 3, FF = 4 };  // FF: float-float pairs (ff.cuh)
 enum class Lk { D18 = 0, F18 = 1, F12 = 2, H12 = 3, FF18 = 4 };
 
@@ -98,9 +103,10 @@ cudaError_t launch_unpack(Sp sp, const FieldRef& in, double2* ext, const Geom& g
                           cudaStream_t st);
 
 // Vector kernels (kinds as in kernels.cuh); x and y formats given separately
+// part_stride: partials per system of a reducing launch (kind 3), 0 for the grid's block count
 cudaError_t launch_vec(Sp spx, Sp spy, const FieldRef& x, const FieldRef& y, size_t n5, int ns, int kind,
                        double coef, SysState* st, int gate, int need, double* partials,
-                       unsigned* counters, int sys_base, int nsys, cudaStream_t stream);
+                       unsigned* counters, int sys_base, int nsys, cudaStream_t stream, int part_stride = 0);
 
 // profiling counter for the next launch_vec (nullptr: none); single-threaded use per call site
 void set_vec_prof(unsigned long long* c);

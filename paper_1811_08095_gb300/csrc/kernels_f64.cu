@@ -97,38 +97,38 @@ void set_vec_prof(unsigned long long* c) { g_vec_prof = c; }
 namespace {
 template <class SX, class SY, class R>
 cudaError_t vec_t(const FieldRef& x, const FieldRef& y, size_t n5, int ns, int kind, double coef, SysState* st,
-                  int gate, int need, double* partials, unsigned* counters, int sys_base, int nsys,
+                  int gate, int need, double* partials, unsigned* counters, int part_stride, int sys_base, int nsys,
                   cudaStream_t stream) {
     dim3 grid(blocks_for(n5, kBS), nsys);
     note_launch(); vec_kernel<SX, SY, R><<<grid, kBS, 0, stream>>>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters,
-                                                    sys_base, g_vec_prof);
+                                                    part_stride, sys_base, g_vec_prof);
     return cudaGetLastError();
 }
 
 template <class SX>
 cudaError_t vec_y(Sp spy, const FieldRef& x, const FieldRef& y, size_t n5, int ns, int kind, double coef,
-                  SysState* st, int gate, int need, double* partials, unsigned* counters, int sys_base,
+                  SysState* st, int gate, int need, double* partials, unsigned* counters, int part_stride, int sys_base,
                   int nsys, cudaStream_t stream) {
     const bool dx = std::is_same<SX, SpF64>::value || std::is_same<SX, SpFF>::value;
     switch (spy) {
         case Sp::F64:
-            return vec_t<SX, SpF64, double>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base,
+            return vec_t<SX, SpF64, double>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, part_stride, sys_base,
                                             nsys, stream);
         case Sp::FF:  // float-float storage, FP64 arithmetic (vector work is a few operations per value)
-            return vec_t<SX, SpFF, double>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base,
+            return vec_t<SX, SpFF, double>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, part_stride, sys_base,
                                            nsys, stream);
         case Sp::F32:
-            if (dx) return vec_t<SX, SpF32, double>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
-            return vec_t<SX, SpF32, float>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base,
+            if (dx) return vec_t<SX, SpF32, double>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, part_stride, sys_base, nsys, stream);
+            return vec_t<SX, SpF32, float>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, part_stride, sys_base,
                                            nsys, stream);
         case Sp::F16:
-            if (dx) return vec_t<SX, SpF16, double>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
-            return vec_t<SX, SpF16, float>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base,
+            if (dx) return vec_t<SX, SpF16, double>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, part_stride, sys_base, nsys, stream);
+            return vec_t<SX, SpF16, float>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, part_stride, sys_base,
                                            nsys, stream);
         case Sp::BF16:
-            if (dx) return vec_t<SX, SpBF16, double>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
+            if (dx) return vec_t<SX, SpBF16, double>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters, part_stride, sys_base, nsys, stream);
             return vec_t<SX, SpBF16, float>(x, y, n5, ns, kind, coef, st, gate, need, partials, counters,
-                                            sys_base, nsys, stream);
+                                            part_stride, sys_base, nsys, stream);
     }
     return cudaErrorInvalidValue;
 }
@@ -136,13 +136,13 @@ cudaError_t vec_y(Sp spy, const FieldRef& x, const FieldRef& y, size_t n5, int n
 
 cudaError_t launch_vec(Sp spx, Sp spy, const FieldRef& x, const FieldRef& y, size_t n5, int ns, int kind,
                        double coef, SysState* st, int gate, int need, double* partials,
-                       unsigned* counters, int sys_base, int nsys, cudaStream_t stream) {
+                       unsigned* counters, int sys_base, int nsys, cudaStream_t stream, int part_stride) {
     switch (spx) {
-        case Sp::F64: return vec_y<SpF64>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
-        case Sp::F32: return vec_y<SpF32>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
-        case Sp::F16: return vec_y<SpF16>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
-        case Sp::BF16: return vec_y<SpBF16>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
-        case Sp::FF: return vec_y<SpFF>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, sys_base, nsys, stream);
+        case Sp::F64: return vec_y<SpF64>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, part_stride, sys_base, nsys, stream);
+        case Sp::F32: return vec_y<SpF32>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, part_stride, sys_base, nsys, stream);
+        case Sp::F16: return vec_y<SpF16>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, part_stride, sys_base, nsys, stream);
+        case Sp::BF16: return vec_y<SpBF16>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, part_stride, sys_base, nsys, stream);
+        case Sp::FF: return vec_y<SpFF>(spy, x, y, n5, ns, kind, coef, st, gate, need, partials, counters, part_stride, sys_base, nsys, stream);
     }
     return cudaErrorInvalidValue;
 }

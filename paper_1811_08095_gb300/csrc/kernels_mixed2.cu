@@ -182,8 +182,8 @@ __global__ void __launch_bounds__(kBS2, 3) hop2_kernel(const HopParams<float> P)
             f32_store_cs<NS>(P.cg_x.d(sys), (size_t)h, s, xv);
         }
     }
-    if (KIND == K2) reduce_and_finalize(nrm, P.partials, P.counters, P.st, sys, FIN_ALPHA);
-    if (KIND == K4) reduce_and_finalize(nrm, P.partials, P.counters, P.st, sys, FIN_BETA);
+    if (KIND == K2) reduce_and_finalize(nrm, P.partials, P.counters, P.st, sys, FIN_ALPHA, P.part_stride);
+    if (KIND == K4) reduce_and_finalize(nrm, P.partials, P.counters, P.st, sys, FIN_BETA, P.part_stride);
 }
 
 // p = r + beta p (mode 1) or p = r (mode 0);  chi = B p.  One thread per (site, s), lane groups of NS.

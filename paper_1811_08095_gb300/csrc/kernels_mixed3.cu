@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(kBS3, hop3_min_blocks<KIND>()) hop3_kernel(con
             pairs_to_mem(upB, dnB, v);
             SpinorIO<SP, float>::store(P.out.d(sys), P.out.n(sys), (size_t)h, s1, NS, v);
         }
-        reduce_and_finalize(nrm, P.partials, P.counters, P.st, sys, FIN_ALPHA);
+        reduce_and_finalize(nrm, P.partials, P.counters, P.st, sys, FIN_ALPHA, P.part_stride);
     } else if (KIND == K3) {
         bidiag2<NS>(upA, dnA, upB, dnB, cf.rho[s0], cf.sigma[s0], cf.rho[s1], cf.sigma[s1], r, l, true);
         minv2<NS>(upA, dnA, upB, dnB, cf, r, l, true, -0.5f);

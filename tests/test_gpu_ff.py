@@ -3,7 +3,7 @@ C ABI.
 
 The reliable update recomputes the true residual b - S^dag S x, in FP64 or in float-float
 arithmetic (each real the unevaluated sum of two FP32 numbers, about 48 bits, on the FP32 pipe);
-by default float-float for a solve of one system and FP64 for batches.
+float-float by default.
 
 * odwf_apply_normal_prec(prec = ODWF_FF), the update's operator with float-float fields, links
   and arithmetic, agrees with the oracle's FP64 S^dag S.  Bar: 1e-10 of the component scale
