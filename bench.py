@@ -784,7 +784,8 @@ def run_hmc(args, world, rank, local):
                       "mass-preconditioned pseudofermion ratios) on 16^3x32x16",
             "value": round(value, 4), "unit": "MD steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_avg, 2), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "%s solves, FP64 forces and updates" % args.prec, "data": "synthetic",
+            "vs_baseline": None, "dtype": "%s solves (%s reliable updates), FP64 forces and MD updates" % (
+                args.prec, update_arith_name(args.updates)), "data": "synthetic",
             "config": {"workload": HMC_WORKLOAD, "lattice": "16^3x32", "Ns": ns, "m0": M0, "beta": HMC_BETA,
                        "mass_chain": list(HMC_CHAIN), "tau": HMC_TAU, "md_steps_per_bench_step": HMC_NSTEPS,
                        "integrator": "Omelyan, Sexton-Weingarten with %d gauge steps per outer drift" % HMC_INNER,
@@ -1012,7 +1013,8 @@ def run_batched_c3(args, world, rank, local):
             "config": {"lattice": "24^3x48", "Ns": NS, "m0": M0, "masses": list(MASSES),
                        "sources": "12 spin-colour point sources at even site %s, wall placement" % (site,),
                        "gauge": "U = exp(0.25 i H) (seed 3)", "prec": args.prec, "link_recon": args.link_recon,
-                       "delta": args.delta, "tol": TOL, "omega": "shifted (R5) Zolotarev on [0.05, 6.2]"}}
+                       "delta": args.delta, "updates": update_arith_name(args.updates), "tol": TOL,
+                       "omega": "shifted (R5) Zolotarev on [0.05, 6.2]"}}
     print(json.dumps(line), flush=True)
     h.close()
 
@@ -1067,7 +1069,8 @@ def run_paper_scale_c5(args, world, rank, local):
             st["n_reliable"], "true_resid": st["true_resid"], "dtype": "f32", "data": "synthetic", "clocks": clk,
             "device_memory": {"used_gb": round((total - free) / 1e9, 2), "total_gb": round(total / 1e9, 2)},
             "config": {"lattice": "64^4", "Ns": NS, "m0": M0, "mq": mq, "gauge": "U = exp(0.2 i H) (seed 5)",
-                       "links": "FP32, 12 reals", "prec": prec, "delta": args.delta, "tol": TOL,
+                       "links": "FP32, 12 reals", "prec": prec, "delta": args.delta,
+                       "updates": update_arith_name(args.updates), "tol": TOL,
                        "rhs": "unit Gaussian (torch seed 5)"}}
     print(json.dumps(line), flush=True)
     h.close()
