@@ -152,3 +152,14 @@ def test_nested_integrator_is_reversible_and_second_order(oracle_lib):
         U1, P1 = hmc.md_nested(U, P, 0.2 / n, n, terms, 6.2, 2)
         dH.append(abs(hmc.hamiltonian(U1, P1, terms, 6.2) - H0))
     assert 3.0 < dH[0] / dH[1] < 5.5, dH
+
+
+def test_kinetic_energy_closed_form():
+    """K = -sum tr P^2 = 1/2 sum_a p_a^2 for P = sum_a p_a T_a, T_a = i lambda_a / 2
+    (tr(lambda_a lambda_b) = 2 delta_ab)."""
+    dims = (2, 2, 2, 4)
+    lx, ly, lz, lt = dims
+    rng = np.random.default_rng(31)
+    p = rng.standard_normal((4, lt, lz, ly, lx, 8))
+    P = np.einsum("...a,aij->...ij", p, 1j * syn.gell_mann() / 2)
+    assert abs(hmc.kinetic(P) - 0.5 * np.sum(p ** 2)) < 1e-12 * np.sum(p ** 2)
