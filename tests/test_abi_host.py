@@ -111,3 +111,20 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libodwf.so"))
     with pytest.raises(RuntimeError, match="no fallback"):
         _lib.load()
+
+
+def test_hmc_entry_points_reject_a_null_handle(lib):
+    """The HMC calls refuse a null handle with ODWF_EINVAL before touching a device."""
+    E = odwf._lib.ODWF_EINVAL
+    act = ctypes.c_double(0.0)
+    prm = odwf._lib.odwf_solve_params()
+    st = odwf._lib.odwf_solve_stats()
+    en = np.zeros(2)
+    assert lib.odwf_pf_force(None, None, 0.1, 0.5, ctypes.byref(prm), ctypes.byref(act), None, ctypes.byref(st),
+                             None) == E
+    assert b"null handle" in lib.odwf_last_error()
+    assert lib.odwf_pf_heatbath(None, None, 0.1, 0.5, ctypes.byref(prm), None, ctypes.byref(st), None) == E
+    assert lib.odwf_gauge_force(None, None, 6.2, ctypes.byref(act), None, None) == E
+    assert lib.odwf_md_trajectory(None, None, None, 0, None, None, None, 6.2, 0.1, 1, 1, 0, ctypes.byref(prm),
+                                  en.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st), None) == E
+    assert b"odwf_md_trajectory" in lib.odwf_last_error()
