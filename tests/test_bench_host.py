@@ -30,3 +30,10 @@ def test_peak_and_single_rank_aggregate():
     assert peak > 1000 and kind in ("measured", "fallback")
     value, t, n = bench.aggregate(2.0, 6)
     assert (value, t, n) == (3.0, 2.0, 6)
+
+
+def test_traffic_of_a_kernel_changed_since_its_capture_is_null():
+    stale = bench.traffic_fields("mixed.f16.l12.v2.K4_normal_cg", 1.7e9)
+    assert stale["traffic"] is None and stale["traffic_prior_capture"] == 1.7e9 and stale["traffic_note"]
+    assert bench.traffic_fields("mixed.f16.l12.v2.K1_chi_minv", 3.8e8) == {"traffic": 3.8e8}
+    assert bench.traffic_fields("mixed.f16.l12.v2.K2_schur_norm_mdinv", None) == {"traffic": None}
